@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 concurrent Delaunay kernel (Mtets/s), one JSON line on stdout.
+
+A step is one complete triangulation (Moore keys, BRIO rounds, radix sort, all insertion
+rounds) of a synthetic cloud resident in HBM. The default workload is 1e7 points i.i.d.
+uniform in the unit cube (float64). `value` is device time measured with CUDA events on the
+library's stream; `e2e` repeats the step through the host entry points with the copies in.
+`--impl reference` times the serial CPU oracle (the reference arm) on a bounded sample.
+Multi-GPU runs are replicas (one independent cloud per rank; a single cloud does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1805_08831_gb300 import synth  # noqa: E402
+
+METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, bit-exact"
+PAPER_1E7_EPYC = 31.3  # Fig. 9, AMD EPYC 7551, 1e7 uniform points (context)
+SEED = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=float, default=1e7)
+    ap.add_argument("--kind", default="uniform", choices=["uniform", "slab", "degenerate"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=float, default=1e6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(kind, n):
+    desc = {"uniform": "i.i.d. uniform in the unit cube",
+            "slab": "70% uniform cube + 30% slab of thickness 1e-3",
+            "degenerate": "40% sphere, 40% Gaussian clusters, 20% lattice"}[kind]
+    return f"{int(n):.0e} points {desc}, float64, seed {SEED}".replace("+0", "")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_bytes(st):
+    """Algorithmic bytes of each round kernel over the run, from the measured C, F, walk steps.
+
+    tetrahedron record 32 B, point 24 B, claim word 8 B (an atomic reads and writes it),
+    index 4 B. Per inserted point with |C| = C, |B| = F, boundary vertices V = F/2 + 2:
+      walk:   per attempt 4 points + 1 record, per step 1 record + 1 new point
+      cavity: records of C and its outside neighbours (F), points of V, claims of C + F,
+              C + F indices out
+      insert: C + F indices in, claims of C + F read, F records read and written, F
+              back-pointers, C freed slots
+    Work of attempts that lost a conflict is overhead, not algorithmic bytes.
+    """
+    ins = max(st["n_unique"], 1)
+    C = st["sum_cavity"] / ins
+    F = st["sum_ball"] / ins
+    V = F / 2 + 2
+    walk = st["n_attempts"] * (4 * 24 + 32) + st["sum_walk"] * (32 + 24)
+    cavity = ins * (32 * (C + F) + 24 * V + 16 * (C + F) + 4 * (C + F))
+    insert = ins * (4 * (C + F) + 8 * (C + F) + 32 * F + 32 * F + 4 * F)
+    return {"walk": walk, "cavity": cavity, "insert": insert}, {"C": C, "F": F, "V": V}
+
+
+def run_oracle(x, seed):
+    import oracle
+    t0 = time.perf_counter()
+    tets, _ = oracle.delaunay(x, seed=seed)
+    return len(tets), time.perf_counter() - t0
+
+
+def cpu_baseline(x_full, sample):
+    m = int(min(sample, len(x_full)))
+    x = np.ascontiguousarray(x_full[:m])
+    ntet, dt_s = run_oracle(x, SEED)
+    return {"value": ntet / dt_s / 1e6, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m} points of the workload, serial CPU oracle (exact predicates), "
+                      f"{ntet} tetrahedra in {dt_s:.2f} s"}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    n = int(args.n)
+    x_full = synth.make(args.kind, n, SEED)
+    m = int(min(2e5, n))
+    x = np.ascontiguousarray(x_full[:m])
+    for _ in range(args.warmup):
+        run_oracle(x, SEED)
+    times, ntet = [], 0
+    for _ in range(args.steps):
+        ntet, t = run_oracle(x, SEED)
+        times.append(t)
+    v = ntet * len(times) / sum(times) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Mtets/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.kind, args.n), "sample_points": m},
+        "cpu_baseline": {"value": v, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {m} points of the workload per step"},
+        "e2e": {"value": v, "unit": "Mtets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import torch
+    import paper_1805_08831_gb300 as dt
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = int(args.n)
+    x_host = synth.make(args.kind, n, SEED + rank)
+    xd = torch.from_numpy(x_host).cuda()
+    stream = torch.cuda.current_stream()
+    flags = 0 if args.no_profile else dt.DT_FLAG_PROFILE
+    tri = dt.Triangulation(seed=SEED, stream=stream, flags=flags)
+    for _ in range(args.warmup):
+        tri.clear()
+        tri.insert(xd)
+    ntet = tri.num_tets()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    totals = {"ms_walk": 0.0, "ms_cavity": 0.0, "ms_insert_k": 0.0, "n_profiled": 0}
+    launches = 0
+    stat_acc = None
+    step_ms = []
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            tri.clear()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tri.insert(xd)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            st = tri.stats()
+            launches += st["n_launches"]
+            for k in totals:
+                totals[k] += st[k]
+            stat_acc = st
+        t_end.record(stream)
+        barrier()
+    clocks = clk.summary()
+    ms = sum(step_ms) / len(step_ms)
+    mine = np.array([sum(step_ms), float(ntet)], dtype=np.float64)
+    if dist is not None:
+        t = torch.tensor(mine, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, all_tets = float(tmax[0]), float(tsum[1])
+    else:
+        total_ms, all_tets = float(mine[0]), float(mine[1])
+    value = all_tets * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the host entry points: pinned input in, tetrahedra out
+    pinned = torch.from_numpy(x_host).pin_memory()
+    e2e_ms = []
+    T = 0
+    for _ in range(max(args.e2e_steps, 1)):
+        tri.clear()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tri.insert_host(pinned.numpy())
+        out = tri.tets_host(canonical=False)
+        t1 = time.perf_counter()
+        T = len(out)
+        e2e_ms.append(1e3 * (t1 - t0))
+    e2e_value = T / (statistics.median(e2e_ms) / 1e3) / 1e6
+    if dist is not None:
+        v = torch.tensor([e2e_value], device="cuda", dtype=torch.float64)
+        dist.all_reduce(v)
+        e2e_value = float(v[0])
+
+    peak, peak_kind = load_peaks()
+    bytes_k, cfb = kernel_bytes(stat_acc)
+    times_k = {"walk": totals["ms_walk"], "cavity": totals["ms_cavity"], "insert": totals["ms_insert_k"]}
+    roofline = None
+    if totals["n_profiled"]:
+        dom = max(times_k, key=lambda k: times_k[k])
+        per_step_ms = times_k[dom] / args.steps
+        achieved = bytes_k[dom] / (per_step_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                    "traffic": None, "share_of_step": per_step_ms / ms,
+                    "kernel_ms_per_step": {k: v / args.steps for k, v in times_k.items()},
+                    "launches_per_step": totals["n_profiled"] / args.steps,
+                    "alg_bytes_per_step": bytes_k[dom]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mtets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_1E7_EPYC if (args.kind == "uniform" and n == 10**7) else None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.kind, n), "n_points": n, "schedule": "plain",
+                   "tets": ntet, "l2": "inputs and tetrahedron store larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "baseline_ref": "paper Fig. 9, AMD EPYC 7551, 1e7 uniform: 31.3 Mtets/s",
+                   "stats": {k: stat_acc[k] for k in ("n_rounds", "n_passes", "n_attempts",
+                                                      "n_conflicts", "n_big", "n_exact", "n_sos")},
+                   "mean_C": cfb["C"], "mean_F": cfb["F"],
+                   "ms_sort": stat_acc["ms_sort"], "ms_insert": stat_acc["ms_insert"]},
+        "e2e": {"value": e2e_value, "unit": "Mtets/s", "h2d_bytes_per_step": n * 24,
+                "d2h_bytes_per_step": T * 16, "ms": statistics.median(e2e_ms)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roofline,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(x_host, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tri.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

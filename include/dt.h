@@ -1,0 +1,161 @@
+/* dt.h — C ABI of the GB300 (sm_103a) concurrent 3D Delaunay kernel.
+ *
+ * The library builds DT(S), the Delaunay triangulation of a 3D point set S, by incremental
+ * Bowyer–Watson insertion as defined in Section 2.1, Eq. (1) of Marot, Pellerin, Remacle,
+ * "One machine, one minute, three billion tetrahedra": DT_{k+1} = DT_k - C(DT_k, p) + B(DT_k, p),
+ * where the cavity C holds every tetrahedron whose circumsphere contains p and the ball B fills
+ * the hole with tetrahedra joining p to the cavity boundary. Many points are inserted
+ * concurrently per round; a point whose cavity overlaps another's (the conflict rules of
+ * Section 3.2) retries in a later round. Because the predicates are exact and degeneracies
+ * are resolved by one symbolic perturbation that depends only on point identity, the result is
+ * the unique perturbed Delaunay triangulation, independent of the schedule.
+ *
+ * Conventions used throughout:
+ *  - points are float64 triples, row-major [n, 3]; coordinates must be finite;
+ *  - vertex ids in outputs are 0-based input indices (global across successive dt_insert calls
+ *    on one handle, local to the cloud in dt_batch);
+ *  - output tetrahedra are finite (ghost tetrahedra of Section 2.6 are dropped) and positively
+ *    oriented, det[b-a; c-a; d-a] > 0; the canonical form rotates each by an even permutation
+ *    so the smallest id is first and the other three start at their smallest, and sorts the
+ *    list lexicographically;
+ *  - exact duplicate points keep the smallest input index; the others are not inserted and are
+ *    counted in dt_stats.n_dups;
+ *  - "device" pointers are CUDA global-memory pointers of the current device; "host" pointers
+ *    are ordinary (preferably pinned) host memory. The caller owns every buffer it passes;
+ *    the library reads inputs during the call (stream-ordered) and copies what it keeps;
+ *  - every function returns DT_OK (0) or a negative DT_E* code, never traps or aborts; device
+ *    loops are bounded and report DT_ELIMIT instead of hanging;
+ *  - a handle is not thread-safe: one host thread at a time.
+ */
+#ifndef DT_GB300_H
+#define DT_GB300_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DT_OK 0
+#define DT_EINVAL (-1)      /* bad argument (null pointer, non-finite coordinate, bad sizes) */
+#define DT_ENOMEM (-2)      /* device allocation failed or tetrahedron capacity exhausted */
+#define DT_ETOOSMALL (-3)   /* output capacity too small; *n_tets holds the required count */
+#define DT_EDEGENERATE (-4) /* fewer than four non-coplanar points */
+#define DT_ELIMIT (-5)      /* a device-side bound tripped (walk, cavity, rounds, exact workspace) */
+#define DT_ECUDA (-6)       /* a CUDA runtime call failed */
+#define DT_ESTATE (-7)      /* call not valid in the handle's current state */
+
+#define DT_SCHED_PLAIN 0    /* Moore segments + rescaling/shift re-partition (Section 3.3) */
+#define DT_SCHED_LEARNED 1  /* segments sized by the learned cavity/conflict model */
+
+#define DT_FLAG_NO_CANONICAL_SORT 1u /* dt_get_tets(canonical=1) rotates but does not sort */
+#define DT_FLAG_PROFILE 2u           /* time each launch of the round kernels with CUDA events */
+
+typedef struct {
+  double tet_capacity_factor; /* tetrahedron slots reserved per point; 0 = 8.0 */
+  uint64_t seed;              /* BRIO hash and re-partition randomness */
+  void* stream;               /* cudaStream_t to run on; NULL = the default stream */
+  uint32_t schedule;          /* DT_SCHED_PLAIN or DT_SCHED_LEARNED */
+  uint32_t max_walk_steps;    /* per walk attempt; 0 = 1 << 16 */
+  uint32_t max_rounds;        /* insertion rounds per call before DT_ELIMIT; 0 = 1 << 22 */
+  uint32_t segments;          /* concurrent insertions per round; 0 = chosen per round */
+  uint32_t flags;             /* DT_FLAG_* */
+  uint32_t reserved[5];       /* must be zero */
+} dt_config;
+
+typedef struct {
+  uint64_t n_points;      /* points given to the handle so far */
+  uint64_t n_unique;      /* points inserted (duplicates excluded) */
+  uint64_t n_dups;        /* exact duplicates not inserted */
+  uint64_t n_tets;        /* finite tetrahedra in the current triangulation */
+  uint64_t n_slots;       /* tetrahedron slots in use (finite + ghost + free) */
+  uint64_t n_rounds;      /* concurrent insertion rounds launched */
+  uint64_t n_passes;      /* re-partition passes (Section 3.3) */
+  uint64_t n_attempts;    /* insertion attempts (successes + retries) */
+  uint64_t n_conflicts;   /* attempts lost to a higher-priority cavity */
+  uint64_t n_big;         /* cavities too large for the shared-memory path */
+  uint64_t sum_cavity;    /* sum of |C| over successful insertions */
+  uint64_t sum_ball;      /* sum of |B| over successful insertions */
+  uint64_t sum_walk;      /* sum of walk steps over all attempts */
+  uint64_t n_exact;       /* predicate evaluations that needed exact arithmetic */
+  uint64_t n_sos;         /* insphere evaluations decided by the perturbation */
+  double ms_sort;         /* device time of keys + sort + dedup (last call) */
+  double ms_insert;       /* device time of the insertion rounds (last call) */
+  uint64_t n_launches;    /* kernels launched by the handle so far */
+  double ms_walk, ms_cavity, ms_insert_k; /* summed launch times of the three round kernels
+                                             (DT_FLAG_PROFILE only) */
+  uint64_t n_profiled;    /* launches of each round kernel that were timed */
+  uint64_t device_error;  /* first device-side error code of the last failing call (0 = none) */
+  uint64_t device_error_info;
+  uint64_t reserved[4];
+} dt_stats;
+
+typedef struct dt_handle dt_handle;
+
+/* Creates an empty triangulation on the current CUDA device. cfg may be NULL (defaults).
+ * *out receives the handle; release it with dt_destroy. */
+int dt_create(dt_handle** out, const dt_config* cfg);
+
+/* Inserts n points (device pointer, [n, 3] float64 row-major) into the handle's triangulation:
+ * Moore keys of the 21-bit quantised coordinates (Section 2.3), BRIO rounds (Table 2 sizes),
+ * radix sort by (round, key, index), then concurrent insertion rounds (Algorithm 1 per point,
+ * Section 3 conflict rules). The first call needs at least four non-coplanar points
+ * (DT_EDEGENERATE otherwise). Later calls extend the same triangulation; the result equals one
+ * call with all points. Input indices of this call start at the number of points given before.
+ * Stream-ordered on cfg->stream; returns after the triangulation is complete. */
+int dt_insert(dt_handle* h, const double* xyz_dev, uint64_t n);
+
+/* Same as dt_insert, with host input: the points are copied to the device inside the call. */
+int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n);
+
+/* Triangulates n_clouds independent clouds in one persistent launch (one cooperative thread
+ * block per cloud at a time). xyz_dev holds the clouds back to back ([sum n_i, 3], device);
+ * offsets_host[c] .. offsets_host[c+1] delimit cloud c (host array of n_clouds + 1 entries,
+ * offsets_host[0] = 0). Replaces the handle's content. Vertex ids are local to each cloud. */
+int dt_batch(dt_handle* h, const double* xyz_dev, const uint64_t* offsets_host, uint32_t n_clouds);
+
+/* Copies the finite tetrahedra of the current triangulation into tets_dev ([cap, 4] uint32,
+ * device). canonical != 0 rotates and sorts them (see conventions); 0 writes them positively
+ * oriented in an unspecified order. *n_tets receives the count; DT_ETOOSMALL if cap < count.
+ * After dt_batch, cloud_offsets (host, n_clouds + 1 entries, may be NULL) receives where each
+ * cloud's tetrahedra start; each cloud's block is canonical on its own. */
+int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets,
+                uint64_t* cloud_offsets, int canonical);
+
+/* Host variant of dt_get_tets: tets_host is host memory. */
+int dt_get_tets_host(dt_handle* h, uint32_t* tets_host, uint64_t cap, uint64_t* n_tets, int canonical);
+
+/* The sort of the last dt_insert call (Section 2.3): keys_dev[i] = 63-bit Moore key of input
+ * point i, perm_dev[s] = input index of the s-th point in (round, key, index) order, and
+ * rounds_dev[i] = BRIO round of point i. Any pointer may be NULL. Indices are call-local. */
+int dt_get_order(dt_handle* h, uint64_t* keys_dev, uint32_t* perm_dev, uint8_t* rounds_dev);
+
+/* Counters of the handle (see dt_stats). */
+int dt_get_stats(dt_handle* h, dt_stats* out);
+
+/* Loads the learned scheduler's parameters (float32, host): W1[8x32], b1[32], W2[32x32], b2[32],
+ * W3[32x2], b3[2] row-major in that order, n_params = 1410. Used when schedule = LEARNED. */
+int dt_load_model(dt_handle* h, const float* params_host, uint32_t n_params);
+
+/* Forgets the triangulation and the points but keeps the device memory, so the next dt_insert
+ * starts a new triangulation without allocating (used between repeated runs). */
+int dt_clear(dt_handle* h);
+
+/* Releases the handle and all its device memory. NULL is a no-op. */
+void dt_destroy(dt_handle* h);
+
+/* Static description of an error code. */
+const char* dt_strerror(int code);
+
+/* Exact predicate signs on the device, for testing the predicates in isolation (Section 2.4):
+ * for each of n tuples, kind 0 = orient3d(a,b,c,d) (4 points), 1 = insphere(a,b,c,d,e) (5 points,
+ * unperturbed), 2 = perturbed insphere with ids_dev giving the 5 point identities.
+ * pts_dev: [n, 5, 3] float64 (unused slots ignored); ids_dev: [n, 5] int64 (kind 2 only, else
+ * NULL); out_dev: [n] int8 signs. */
+int dt_eval_predicates(int kind, const double* pts_dev, const int64_t* ids_dev, int8_t* out_dev,
+                       uint64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,557 @@
+// Device side of concurrent Bowyer-Watson insertion (Algorithm 1 per point, Section 3 rules).
+//
+// One insertion round processes R candidate points in three phases separated by kernel
+// boundaries (or block barriers), so every read of the triangulation in phases 1-2 sees the
+// same state:
+//   1. walk (thread per point): visibility walk with orient3d (Section 2.1, ghost rules of
+//      Section 2.6) to a tetrahedron in conflict with p;
+//   2. cavity (warp per point): breadth-first search over tetrahedra in conflict (perturbed
+//      insphere, composite ghost sphere), recording the cavity C and its boundary facets; every
+//      tetrahedron of C and of its outside neighbours A is claimed with atomicMax of a
+//      priority (round stamp << 32 | point id + 1);
+//   3. insert (warp per point): a point whose claims on C and A all survived owns them
+//      (rules (1a)(1b) of Section 3.2: winners' C u A sets are disjoint) and replaces C by
+//      the ball B (Section 2.5): one tetrahedron per boundary facet, the cavity tetrahedron
+//      with its vertex opposite the facet replaced by p, adjacency to the outside tetrahedron
+//      known a priori, adjacencies between new tetrahedra through the n x n edge table of
+//      oriented boundary edges (hash fallback for large cavities), slots taken from the
+//      cavity first, then from the free list, then from the bump pointer (rule (2)).
+// The highest-priority located point of a round always wins, so every round makes progress.
+#pragma once
+#include "common.cuh"
+#include "predicates.cuh"
+
+namespace dtg {
+
+enum CandStatus : uint32_t {
+  kCandEmpty = 0,
+  kCandLocated = 1,
+  kCandWalkLimit = 2,
+  kCandDup = 3,
+  kCandLost = 4,
+  kCandBig = 5,
+  kCandInserted = 6,
+};
+
+constexpr int kCMax = 64;   // cavity tetrahedra on the shared-memory path
+constexpr int kFMax = 60;   // boundary facets on the shared-memory path (<= 32 boundary vertices)
+constexpr int kHash = 256;  // visited-set slots per warp (shared-memory path)
+
+struct Ctx {
+  Tet* tets;
+  unsigned long long* claim;
+  const Pt* pts;  // .w = input index (the perturbation order)
+  uint32_t* freelist;
+  uint32_t* pending;
+  uint32_t* cell_hint;
+  uint32_t* point_hint;
+  DevState* st;
+  double lo[3], sc[3];
+  int cb;  // bits per axis of the hint grid
+  uint32_t max_walk;
+  int coherent;  // 1 when this kernel also writes the tetrahedra it reads (L2 loads)
+  uint32_t ntets;  // tetrahedron slots allocated (bounds of every id read from the mesh)
+  uint32_t npts;   // vertex slots allocated
+};
+
+// A tetrahedron record read from the mesh only references allocated vertices and slots; a
+// record that does not raises kErrInternal (the kernels then stop using it) instead of
+// letting a bad id reach memory.
+__device__ __forceinline__ bool tet_sane(const Ctx& c, const Tet& T) {
+  bool ok = true;
+  for (int k = 0; k < 4; ++k) {
+    uint32_t v = get4(T.v, k), n = get4(T.n, k);
+    ok = ok && (v == kGhost || v < c.npts) && (n >> 2) < c.ntets;
+  }
+  return ok;
+}
+
+__device__ __forceinline__ Tet tet_at(const Ctx& c, uint32_t t) {
+  return c.coherent ? load_tet_cg(c.tets, t) : load_tet(c.tets, t);
+}
+
+__device__ __forceinline__ uint32_t nbr_at(const Ctx& c, uint32_t t, int f) {
+  const uint32_t* p = reinterpret_cast<const uint32_t*>(&c.tets[t].n) + f;
+  return c.coherent ? __ldcg(p) : __ldg(p);
+}
+
+// Working storage of one cavity search (shared memory per warp, or global for large cavities).
+struct CavWS {
+  uint32_t* hkey;
+  uint8_t* hval;  // 1 = in cavity, 2 = outside
+  uint32_t hmask;
+  uint32_t* clist;
+  uint32_t cmax;
+  uint32_t* blist;  // boundary facets as 4 * (cavity tetrahedron) + facet
+  uint32_t bmax;
+};
+
+// Working storage of one ball construction.
+struct InsWS {
+  uint4* nv;
+  uint4* nn;  // neighbours of the new tetrahedra, validated before anything is written
+  uint32_t* outh;
+  uint32_t* slot;
+  uint8_t* ipos;
+  uint32_t* vkey;  // 32-slot vertex hash: slot = cavity-local vertex index
+  uint16_t* tab;   // 32 x 32 edge table
+  unsigned long long* ekey;
+  uint32_t* eval;
+  uint32_t* hslot;
+  uint32_t* hold;
+  uint32_t emask;
+};
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t cell_of(const Ctx& c, Pt P) {
+  double x[3] = {P.x, P.y, P.z};
+  double lim = (double)((1u << c.cb) - 1u);
+  uint32_t q[3];
+  for (int k = 0; k < 3; ++k) {
+    double f = floor((x[k] - c.lo[k]) * c.sc[k]);
+    f = f < 0.0 ? 0.0 : (f > lim ? lim : f);
+    q[k] = (uint32_t)f;
+  }
+  return (q[2] << (2 * c.cb)) | (q[1] << c.cb) | q[0];
+}
+
+// Positions (a, b, c) such that (p, w[a], w[b], w[c]) is an even permutation of a tetrahedron
+// w with p at position i.
+// i = 0: (1,2,3); 1: (0,3,2); 2: (0,1,3); 3: (0,2,1).
+__device__ __forceinline__ void after_pos(int i, int& a, int& b, int& c) {
+  a = (i == 0) ? 1 : 0;
+  b = (i == 0) ? 2 : (i == 1) ? 3 : (i == 2) ? 1 : 2;
+  c = (i == 0) ? 3 : (i == 1) ? 2 : (i == 2) ? 3 : 1;
+}
+
+__device__ __forceinline__ Pt sel4(int i, int k, Pt P, Pt V) { return i == k ? P : V; }
+
+// ------------------------------------------------------------------ walk (Section 2.1)
+// Returns kCandLocated (*t_out in conflict with P), kCandWalkLimit (*t_out = where it stopped)
+// or kCandDup (P equals a vertex of the tetrahedron reached).
+__device__ int walk_point(const Ctx& c, Pt P, uint32_t start, uint32_t salt, uint32_t anchor,
+                          uint32_t max_steps, uint32_t* t_out, uint32_t* steps_out) {
+  uint32_t t = start;
+  Tet T;
+  int hops = 0;
+  for (;;) {
+    if (t == kNone || t >= c.ntets) t = anchor;
+    T = tet_at(c, t);
+    if (!tet_dead(T.v)) break;
+    t = (++hops > 64) ? anchor : T.n.x;  // dead slot: follow the redirect it keeps
+    if (t != kNone && t >= c.ntets) t = anchor;
+    if (hops > 66) {
+      raise_error(c.st, kErrWalk, t);
+      *t_out = anchor;
+      *steps_out = 0;
+      return kCandWalkLimit;
+    }
+  }
+  if (!tet_sane(c, T)) {
+    raise_error(c.st, kErrInternal, 0xA000u);
+    *t_out = anchor;
+    *steps_out = 0;
+    return kCandWalkLimit;
+  }
+  int g = ghost_pos(T.v);
+  if (g >= 0) {  // a ghost start steps into its real neighbour (Section 2.6)
+    t = get4(T.n, g) >> 2;
+    T = tet_at(c, t);
+    if (!tet_sane(c, T)) {
+      raise_error(c.st, kErrInternal, 0xA001u);
+      *t_out = anchor;
+      *steps_out = 0;
+      return kCandWalkLimit;
+    }
+  }
+  uint32_t prev = kNone;
+  uint32_t steps = 0;
+  Pt V0, V1, V2, V3;
+  for (;;) {
+    if (ghost_pos(T.v) >= 0) break;  // entered a ghost through a facet that sees P
+    V0 = load_pt(c.pts, T.v.x);
+    V1 = load_pt(c.pts, T.v.y);
+    V2 = load_pt(c.pts, T.v.z);
+    V3 = load_pt(c.pts, T.v.w);
+    int exit = -1;
+    int s0 = (salt + steps) & 3;
+    for (int k = 0; k < 4; ++k) {
+      int i = (s0 + k) & 3;
+      uint32_t nb = get4(T.n, i) >> 2;
+      if (nb == prev) continue;  // P is on this tetrahedron's side of the facet just crossed
+      int o = orient3d(sel4(i, 0, P, V0), sel4(i, 1, P, V1), sel4(i, 2, P, V2), sel4(i, 3, P, V3), c.st);
+      if (o < 0) {
+        exit = i;
+        break;
+      }
+    }
+    if (exit < 0) {
+      bool dup = (V0.x == P.x && V0.y == P.y && V0.z == P.z) || (V1.x == P.x && V1.y == P.y && V1.z == P.z) ||
+                 (V2.x == P.x && V2.y == P.y && V2.z == P.z) || (V3.x == P.x && V3.y == P.y && V3.z == P.z);
+      *t_out = t;
+      *steps_out = steps;
+      return dup ? kCandDup : kCandLocated;
+    }
+    if (steps >= max_steps) {
+      *t_out = t;
+      *steps_out = steps;
+      return kCandWalkLimit;
+    }
+    prev = t;
+    t = get4(T.n, exit) >> 2;
+    T = tet_at(c, t);
+    ++steps;
+    if (!tet_sane(c, T) || tet_dead(T.v)) {
+      raise_error(c.st, kErrInternal, 0xA002u);
+      *t_out = anchor;
+      *steps_out = steps;
+      return kCandWalkLimit;
+    }
+  }
+  *t_out = t;
+  *steps_out = steps;
+  return kCandLocated;
+}
+
+// ------------------------------------------------------------------ conflict test
+// Membership of tetrahedron u in the cavity of P: perturbed insphere for a finite tetrahedron;
+// for a ghost, P strictly beyond its hull facet, or on the facet's plane and inside the
+// perturbed sphere of the finite neighbour across it (Section 2.6).
+__device__ bool in_conflict(const Ctx& c, uint32_t u, Pt P) {
+  Tet U = tet_at(c, u);
+  if (!tet_sane(c, U) || tet_dead(U.v)) {
+    raise_error(c.st, kErrInternal, 0xB000u);
+    return false;
+  }
+  int g = ghost_pos(U.v);
+  if (g < 0) {
+    Pt a = load_pt(c.pts, U.v.x), b = load_pt(c.pts, U.v.y), d = load_pt(c.pts, U.v.z),
+            e = load_pt(c.pts, U.v.w);
+    return insphere_sos(a, b, d, e, P, c.st) < 0;
+  }
+  Pt q[4];
+  for (int k = 0; k < 4; ++k) q[k] = (k == g) ? P : load_pt(c.pts, get4(U.v, k));
+  int o = orient3d(q[0], q[1], q[2], q[3], c.st);
+  if (o != 0) return o > 0;
+  uint32_t r = get4(U.n, g) >> 2;
+  Tet R = tet_at(c, r);
+  if (!tet_sane(c, R) || ghost_pos(R.v) >= 0) {
+    raise_error(c.st, kErrInternal, 0xB001u);
+    return false;
+  }
+  Pt a = load_pt(c.pts, R.v.x), b = load_pt(c.pts, R.v.y), d = load_pt(c.pts, R.v.z),
+          e = load_pt(c.pts, R.v.w);
+  return insphere_sos(a, b, d, e, P, c.st) < 0;
+}
+
+// ------------------------------------------------------------------ visited set
+__device__ __forceinline__ uint32_t hash32(uint32_t k) { return k * 0x9E3779B1u; }
+
+__device__ __forceinline__ int ws_find(const CavWS& w, uint32_t key) {
+  uint32_t h = (hash32(key) >> 8) & w.hmask;
+  for (uint32_t probe = 0; probe <= w.hmask; ++probe) {
+    uint32_t k = w.hkey[h];
+    if (k == key) return w.hval[h];
+    if (k == kNone) return 0;
+    h = (h + 1) & w.hmask;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ bool ws_insert(const CavWS& w, uint32_t key, uint8_t val) {
+  uint32_t h = (hash32(key) >> 8) & w.hmask;
+  for (uint32_t probe = 0; probe <= w.hmask; ++probe) {
+    uint32_t old = atomicCAS(&w.hkey[h], kNone, key);
+    if (old == kNone || old == key) {
+      w.hval[h] = val;
+      return true;
+    }
+    h = (h + 1) & w.hmask;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ cavity (warp)
+// Returns kCandLocated (C in w.clist[0..nc), boundary facets in w.blist[0..nb)), kCandLost
+// (saw a higher-priority claim) or kCandBig (exceeds this workspace).
+__device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, Pt P,
+                           unsigned long long prio, int* nc_out, int* nb_out) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t i = lane; i <= w.hmask; i += 32) w.hkey[i] = kNone;
+  __syncwarp();
+  int flag = 0;  // 1 lost, 2 big, 4 internal
+  if (lane == 0) {
+    if (!in_conflict(c, t0, P)) flag |= 4;
+    w.clist[0] = t0;
+    ws_insert(w, t0, 1);
+    if (atomicMax(&c.claim[t0], prio) > prio) flag |= 1;
+  }
+  flag = __shfl_sync(kFull, flag, 0);
+  if (flag & 4) {
+    if (lane == 0) raise_error(c.st, kErrInternal, t0);
+    return kCandLost;
+  }
+  __syncwarp();
+  int nc = 1, nb = 0, head = 0;
+  while (head < nc && flag == 0) {
+    int batch = min(8, nc - head);
+    int k = lane >> 2, f = lane & 3;
+    bool active = k < batch;
+    uint32_t t = 0, u = kNone;
+    if (active) {
+      t = w.clist[head + k];
+      u = nbr_at(c, t, f) >> 2;
+      if (u >= c.ntets) {
+        raise_error(c.st, kErrInternal, 0xC000u);
+        u = t;
+      }
+    }
+    head += batch;
+    int known = active ? ws_find(w, u) : 0;
+    bool need = active && known == 0;
+    unsigned peers = __match_any_sync(kFull, need ? u : 0xFFFFFFFFu);
+    int leader = __ffs(peers) - 1;
+    bool is_leader = need && lane == leader;
+    int res = 0, myflag = 0;
+    if (is_leader) {
+      res = in_conflict(c, u, P) ? 1 : 2;
+      if (atomicMax(&c.claim[u], prio) > prio) myflag |= 1;
+      if (!ws_insert(w, u, (uint8_t)res)) myflag |= 2;
+    }
+    int lres = __shfl_sync(kFull, res, leader);
+    if (need) res = lres;
+    else res = known;
+    bool addC = is_leader && res == 1;
+    unsigned mC = __ballot_sync(kFull, addC);
+    if (addC) {
+      int pos = nc + __popc(mC & lanemask_lt());
+      if (pos < (int)w.cmax) w.clist[pos] = u;
+    }
+    nc += __popc(mC);
+    bool addB = active && res == 2;
+    unsigned mB = __ballot_sync(kFull, addB);
+    if (addB) {
+      int pos = nb + __popc(mB & lanemask_lt());
+      if (pos < (int)w.bmax) w.blist[pos] = 4 * t + f;
+    }
+    nb += __popc(mB);
+    flag = __reduce_or_sync(kFull, myflag);
+    if (nc > (int)w.cmax || nb > (int)w.bmax) flag |= 2;
+    if (__ldcg(&c.st->error) != 0u) flag |= 1;  // stop on any raised error
+    __syncwarp();
+  }
+  *nc_out = nc;
+  *nb_out = nb;
+  if (flag & 1) return kCandLost;
+  if (flag & 2) return kCandBig;
+  return kCandLocated;
+}
+
+// ------------------------------------------------------------------ slot allocation
+// Virtual slot v of this round: the free list (top first), then the bump pointer.
+__device__ __forceinline__ uint32_t virtual_slot(const Ctx& c, unsigned long long v,
+                                                 unsigned long long fa, unsigned long long bump,
+                                                 unsigned long long cap, bool& fail) {
+  if (v < fa) return c.freelist[fa - 1 - v];
+  unsigned long long b = bump + (v - fa);
+  if (b >= cap) {
+    fail = true;
+    return kNone;
+  }
+  return (uint32_t)b;
+}
+
+// Empty slot of the vertex hash: never a vertex id (the ghost vertex is kGhost = kNone).
+constexpr uint32_t kNoVertex = kDeadMark;
+
+__device__ __forceinline__ int vslot(uint32_t* vkey, uint32_t x) {
+  uint32_t h = hash32(x) >> 27;
+  for (int probe = 0; probe < 32; ++probe) {
+    uint32_t old = atomicCAS(&vkey[h], kNoVertex, x);
+    if (old == kNoVertex || old == x) return (int)h;
+    h = (h + 1) & 31u;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ uint32_t edge_slot(const InsWS& w, unsigned long long key) {
+  uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & w.emask;
+  for (uint32_t probe = 0; probe <= w.emask; ++probe) {
+    unsigned long long old = atomicCAS(&w.ekey[h], ~0ull, key);
+    if (old == ~0ull || old == key) return h;
+    h = (h + 1) & w.emask;
+  }
+  return kNone;
+}
+
+// ------------------------------------------------------------------ ball (warp)
+// Verifies the claims of a located point and, if it won, replaces its cavity by the ball.
+// Returns kCandInserted or kCandLost. alloc: allocator snapshot of this round.
+__device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned long long prio,
+                           const uint32_t* clist, int nc, const uint32_t* blist, int nb,
+                           bool use_table, unsigned long long fa, unsigned long long bump,
+                           unsigned long long cap) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int i = lane; i < nc; i += 32)
+    if (__ldcg(&c.claim[clist[i]]) != prio) ok = false;
+  if (!__all_sync(kFull, ok)) return kCandLost;
+  for (int i = lane; i < nb; i += 32) {
+    uint32_t e = blist[i];
+    uint32_t t = e >> 2;
+    int f = (int)(e & 3u);
+    Tet T = load_tet_cg(c.tets, t);
+    uint32_t out = get4(T.n, f);
+    if ((out >> 2) >= c.ntets || !tet_sane(c, T)) {
+      raise_error(c.st, kErrInternal, 0xD000u);
+      ok = false;
+      out = 0;
+    }
+    if (__ldcg(&c.claim[out >> 2]) != prio) ok = false;
+    uint4 v = T.v;
+    set4(v, f, p);
+    w.nv[i] = v;
+    w.outh[i] = out;
+    w.ipos[i] = (uint8_t)f;
+  }
+  if (!__all_sync(kFull, ok)) return kCandLost;
+  // slots: cavity slots first (Section 2.5), then the allocator (Section 3.6)
+  int reuse = min(nc, nb), extra = nb - reuse;
+  unsigned long long base = 0;
+  if (lane == 0 && extra > 0) base = atomicAdd(&c.st->alloc_cursor, (unsigned long long)extra);
+  base = __shfl_sync(kFull, base, 0);
+  bool fail = false;
+  for (int i = lane; i < nb; i += 32)
+    w.slot[i] = (i < reuse) ? clist[i] : virtual_slot(c, base + (unsigned long long)(i - reuse), fa, bump, cap, fail);
+  if (__any_sync(kFull, fail)) {
+    if (lane == 0) raise_error(c.st, kErrCapacity, (unsigned)nb);
+    return kCandLost;
+  }
+  if (use_table)
+    for (int i = lane; i < 32; i += 32) w.vkey[i] = kNoVertex;
+  else
+    for (uint32_t i = lane; i <= w.emask; i += 32) {
+      w.ekey[i] = ~0ull;
+      w.eval[i] = kNone;
+    }
+  __syncwarp();
+  // record every internal facet: facet a of new tetrahedron i holds the boundary edge b -> c
+  if (use_table) {
+    bool vfail = false;
+    for (int i = lane; i < nb; i += 32) {
+      uint4 v = w.nv[i];
+      int a, b, cc;
+      after_pos(w.ipos[i], a, b, cc);
+      int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
+      if (la < 0 || lb < 0 || lc < 0) {
+        vfail = true;
+        continue;
+      }
+      w.tab[lb * 32 + lc] = (uint16_t)((i << 2) | a);
+      w.tab[lc * 32 + la] = (uint16_t)((i << 2) | b);
+      w.tab[la * 32 + lb] = (uint16_t)((i << 2) | cc);
+    }
+    if (__any_sync(kFull, vfail)) {
+      if (lane == 0) raise_error(c.st, kErrInternal, 0x7AB1u);
+      return kCandLost;
+    }
+  } else {
+    bool efail = false;
+    for (int i = lane; i < nb; i += 32) {
+      uint4 v = w.nv[i];
+      int pos[3];
+      after_pos(w.ipos[i], pos[0], pos[1], pos[2]);
+      for (int k = 0; k < 3; ++k) {
+        uint32_t x = get4(v, pos[(k + 1) % 3]), y = get4(v, pos[(k + 2) % 3]);
+        unsigned long long key = ((unsigned long long)min(x, y) << 32) | max(x, y);
+        uint32_t s = edge_slot(w, key);
+        if (s == kNone) {
+          efail = true;
+          break;
+        }
+        w.hslot[3 * i + k] = s;
+        w.hold[3 * i + k] = atomicExch(&w.eval[s], (uint32_t)((i << 2) | pos[k]));
+      }
+    }
+    if (__any_sync(kFull, efail)) {
+      if (lane == 0) raise_error(c.st, kErrBigCavity, (unsigned)nb);
+      return kCandLost;
+    }
+  }
+  __syncwarp();
+  // partners of every internal facet; all must name a new tetrahedron before any write
+  bool bad = false;
+  for (int i = lane; i < nb; i += 32) {
+    uint4 v = w.nv[i];
+    int ip = w.ipos[i];
+    int a, b, cc;
+    after_pos(ip, a, b, cc);
+    uint32_t ea, eb, ec;
+    if (use_table) {
+      int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
+      ea = w.tab[lc * 32 + lb];
+      eb = w.tab[la * 32 + lc];
+      ec = w.tab[lb * 32 + la];
+    } else {
+      uint32_t hh[3];
+      for (int k = 0; k < 3; ++k) {
+        uint32_t old = w.hold[3 * i + k];
+        hh[k] = (old != kNone) ? old : w.eval[w.hslot[3 * i + k]];
+      }
+      ea = hh[0];
+      eb = hh[1];
+      ec = hh[2];
+    }
+    if ((ea >> 2) >= (uint32_t)nb || (eb >> 2) >= (uint32_t)nb || (ec >> 2) >= (uint32_t)nb ||
+        (ea >> 2) == (uint32_t)i || (eb >> 2) == (uint32_t)i || (ec >> 2) == (uint32_t)i) {
+      bad = true;
+      continue;
+    }
+    uint4 nn;
+    set4(nn, ip, w.outh[i]);
+    set4(nn, a, 4u * w.slot[ea >> 2] + (ea & 3u));
+    set4(nn, b, 4u * w.slot[eb >> 2] + (eb & 3u));
+    set4(nn, cc, 4u * w.slot[ec >> 2] + (ec & 3u));
+    w.nn[i] = nn;
+  }
+  if (__any_sync(kFull, bad)) {
+    if (lane == 0) raise_error(c.st, kErrInternal, 0xE000u);
+    return kCandLost;
+  }
+  __syncwarp();
+  // write the ball
+  for (int i = lane; i < nb; i += 32) {
+    uint32_t s = w.slot[i];
+    uint4* dst = reinterpret_cast<uint4*>(c.tets + s);
+    dst[0] = w.nv[i];
+    dst[1] = w.nn[i];
+    uint32_t out = w.outh[i];
+    reinterpret_cast<uint32_t*>(&c.tets[out >> 2].n)[out & 3u] = 4u * s + (uint32_t)w.ipos[i];
+  }
+  // cavity slots left over (|C| > |B|) die and join the free list after the round
+  int freed = nc - nb;
+  if (freed > 0) {
+    unsigned long long pb = 0;
+    if (lane == 0) pb = atomicAdd(&c.st->pending, (unsigned long long)freed);
+    pb = __shfl_sync(kFull, pb, 0);
+    uint32_t redirect = w.slot[0];
+    for (int i = lane; i < freed; i += 32) {
+      uint32_t s = clist[nb + i];
+      uint4* dst = reinterpret_cast<uint4*>(c.tets + s);
+      dst[0] = make_uint4(kDeadMark, kDeadMark, kDeadMark, kDeadMark);
+      dst[1] = make_uint4(redirect, kNone, kNone, kNone);
+      if (pb + i < c.st->free_capacity) c.pending[pb + i] = s;
+      else raise_error(c.st, kErrFreeList, 0);
+    }
+  }
+  return kCandInserted;
+}
+
+}  // namespace dtg

@@ -1,0 +1,170 @@
+"""GPU path vs the CPU oracle, through the C ABI (bit-exact: integer and index results)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_08831_gb300 import synth
+from tests.inputs import DEGENERATE_SETS
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1805_08831_gb300 as dt  # noqa: E402
+
+
+def gpu_tets(x, seed=0, **kw):
+    xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+    with dt.Triangulation(seed=seed, **kw) as t:
+        t.insert(xt)
+        tets = t.tets_numpy(canonical=True)
+        st = t.stats()
+    return tets, st
+
+
+def assert_same(a, b):
+    assert a.shape == b.shape, (a.shape, b.shape)
+    if not np.array_equal(a, b):
+        bad = np.nonzero((a != b).any(axis=1))[0]
+        raise AssertionError(f"{len(bad)} rows differ; first at {bad[:5]}: {a[bad[:3]]} vs {b[bad[:3]]}")
+
+
+# ----------------------------------------------------------------------------- predicates
+def _tuples(rng, n):
+    p = rng.random((n, 5, 3))
+    kind = rng.integers(0, 4, n)
+    for i in np.nonzero(kind == 1)[0]:  # box corners: exactly co-spherical
+        lo, hi = rng.random(3), rng.random(3) + 1.0
+        c = np.array([[hi[0] if j & 1 else lo[0], hi[1] if j & 2 else lo[1], hi[2] if j & 4 else lo[2]]
+                      for j in range(8)])
+        p[i] = c[rng.permutation(8)[:5]]
+    for i in np.nonzero(kind == 2)[0]:  # four points on an axis plane
+        p[i, :4, 2] = p[i, 0, 2]
+    for i in np.nonzero(kind == 3)[0]:  # one-ulp nudge of a co-spherical set
+        lo, hi = rng.random(3), rng.random(3) + 1.0
+        c = np.array([[hi[0] if j & 1 else lo[0], hi[1] if j & 2 else lo[1], hi[2] if j & 4 else lo[2]]
+                      for j in range(8)])
+        p[i] = c[rng.permutation(8)[:5]]
+        p[i, 4, 0] = np.nextafter(p[i, 4, 0], 10.0)
+    return p
+
+
+def test_device_predicates_match_oracle():
+    rng = np.random.default_rng(3)
+    n = 4000
+    p = _tuples(rng, n)
+    ids = np.stack([rng.permutation(100)[:5] for _ in range(n)]).astype(np.int64)
+    pt = torch.from_numpy(p).cuda()
+    it = torch.from_numpy(ids).cuda()
+    o = dt.eval_predicates(0, pt).cpu().numpy()
+    s = dt.eval_predicates(1, pt).cpu().numpy()
+    q = dt.eval_predicates(2, pt, it).cpu().numpy()
+    for i in range(n):
+        assert o[i] == oracle.orient3d(*p[i, :4]), i
+        assert s[i] == oracle.insphere(*p[i]), i
+        if oracle.orient3d(*p[i, :4]) > 0:
+            assert q[i] == oracle.insphere_sos(p[i], ids[i]), i
+
+
+# ----------------------------------------------------------------------------- order
+@pytest.mark.parametrize("n", [1, 5, 2047, 2049, 14337, 100000])
+def test_moore_keys_and_insertion_order(n):
+    x = synth.uniform_cube(n, 21)
+    x[n // 2:n // 2 + min(5, n // 4)] = x[:min(5, n // 4)]  # duplicates share a key
+    xt = torch.from_numpy(x).cuda()
+    with dt.Triangulation(seed=99) as t:
+        try:
+            t.insert(xt)
+        except dt.DTError as e:
+            assert e.code == dt.DT_EDEGENERATE and n < 4
+            return
+        keys, perm, rounds = t.order(n)
+    assert np.array_equal(keys, oracle.moore_keys(x))
+    assert np.array_equal(rounds, oracle.brio_rounds(n, 99))
+    assert np.array_equal(perm, oracle.insertion_order(x, 99))
+
+
+# ----------------------------------------------------------------------------- triangulations
+@pytest.mark.parametrize("name", sorted(DEGENERATE_SETS))
+def test_degenerate_sets(name):
+    x = DEGENERATE_SETS[name]
+    ref, _ = oracle.delaunay(x)
+    got, _ = gpu_tets(x)
+    assert_same(got, ref)
+
+
+@pytest.mark.parametrize("n", [4, 5, 7, 30, 200, 2047, 2049, 20000])
+def test_uniform_small_and_ragged(n):
+    x = synth.uniform_cube(n, 1000 + n)
+    ref, _ = oracle.delaunay(x, seed=5)
+    got, _ = gpu_tets(x, seed=5)
+    assert_same(got, ref)
+
+
+def test_uniform_1e5_bit_exact():
+    x = synth.uniform_cube(100000, 1)
+    ref, _ = oracle.delaunay(x, seed=1)
+    got, st = gpu_tets(x, seed=1)
+    assert_same(got, ref)
+    assert st["n_unique"] == 100000 and st["n_exact"] == 0
+
+
+def test_degenerate_mix_bit_exact():
+    x = synth.degenerate_mix(30000, 3)
+    x[-3000:] = x[-6000:-3000]  # repeated lattice sites
+    ref, ost = oracle.delaunay(x, seed=3)
+    got, st = gpu_tets(x, seed=3)
+    assert_same(got, ref)
+    assert st["n_unique"] == ost["n_unique"]
+
+
+def test_slab_bit_exact():
+    x = synth.cube_and_slab(30000, 5)
+    ref, _ = oracle.delaunay(x, seed=2)
+    got, _ = gpu_tets(x, seed=2)
+    assert_same(got, ref)
+
+
+def test_schedule_does_not_change_tets():
+    x = synth.uniform_cube(20000, 8)
+    ref, _ = oracle.delaunay(x, seed=1)
+    for seg in (1, 7, 64, 4096):
+        got, _ = gpu_tets(x, seed=1, segments=seg)
+        assert_same(got, ref)
+    got, _ = gpu_tets(x, seed=12345)
+    assert_same(got, ref)
+
+
+def test_successive_inserts_extend_the_triangulation():
+    x = synth.uniform_cube(12000, 17)
+    x[11000:11010] = x[100:110]  # duplicates across calls keep the earlier (smaller) index
+    ref, _ = oracle.delaunay(x, seed=4)
+    with dt.Triangulation(seed=4) as t:
+        t.insert(torch.from_numpy(x[:5000]).cuda())
+        t.insert(torch.from_numpy(x[5000:]).cuda())
+        got = t.tets_numpy()
+        st = t.stats()
+    assert_same(got, ref)
+    assert st["n_points"] == 12000 and st["n_unique"] == 11990
+
+
+def test_host_entry_points_match_device_ones():
+    x = synth.uniform_cube(5000, 6)
+    ref, _ = oracle.delaunay(x)
+    with dt.Triangulation() as t:
+        t.insert_host(x)
+        assert_same(t.tets_host(), ref)
+
+
+def test_errors_are_reported_not_raised_on_device():
+    plane = np.c_[synth.uniform_cube(100, 1)[:, :2], np.zeros(100)]
+    with pytest.raises(dt.DTError) as e:
+        gpu_tets(plane)
+    assert e.value.code == dt.DT_EDEGENERATE
+    bad = synth.uniform_cube(100, 1)
+    bad[7, 2] = np.inf
+    with pytest.raises(dt.DTError) as e:
+        gpu_tets(bad)
+    assert e.value.code == dt.DT_EINVAL

@@ -57,6 +57,7 @@ class Stats(ctypes.Structure):
             d[f] = getattr(self, f)
         d["n_walk_limit"] = self.reserved[0]
         d["free_slots"] = self.reserved[1]
+        d["max_walk"] = self.reserved[2]
         return d
 
 

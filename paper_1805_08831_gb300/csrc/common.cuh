@@ -56,15 +56,17 @@ struct DevState {
   unsigned long long alloc_cursor;   // virtual allocation cursor of this round
   unsigned long long pending;        // slots freed this round (appended after the round)
   unsigned long long free_capacity;  // size of the free-list array
-  unsigned long long qnext;          // points queued for the next pass
-  unsigned long long nbig;           // points queued for the large-cavity path
+  unsigned long long q[4];           // queue lengths: 0 next pass, 1 large cavities,
+                                     // 2 large-cavity retries, 3 serial path
+  unsigned int blocks_done;          // blocks of the insert kernel that finished this round
+  unsigned int pad1;
   unsigned int error;                // first DevError raised
   unsigned int error_info;
   unsigned int anchor;               // a tetrahedron known to be live
   unsigned int pad0;
   // statistics
   unsigned long long n_inserted, n_conflicts, n_attempts, n_walk_limit, n_big, n_dups;
-  unsigned long long sum_cavity, sum_ball, sum_walk, n_exact, n_sos;
+  unsigned long long sum_cavity, sum_ball, sum_walk, n_exact, n_sos, max_walk;
 };
 
 __device__ __forceinline__ void raise_error(DevState* st, unsigned int code, unsigned int info) {

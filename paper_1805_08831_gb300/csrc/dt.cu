@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -19,42 +20,114 @@ namespace {
 constexpr int kWarps = 8;  // candidates per 256-thread block in the warp-per-point kernels
 constexpr uint32_t kScratchStride = kCMax + kFMax;
 
-// Large-cavity workspace capacities (global memory, one point at a time).
-constexpr uint32_t kBigHash = 1u << 17;
-constexpr uint32_t kBigC = 1u << 15;
-constexpr uint32_t kBigF = 1u << 15;
-constexpr uint32_t kBigEdge = 1u << 17;
+// Queues of points a round hands on (DevState::q).
+constexpr int kQNext = 0;   // lost a conflict or hit the walk limit: next pass
+constexpr int kQBig = 1;    // cavity too large for shared memory: large-cavity rounds
+constexpr int kQBig2 = 2;   // lost a conflict in a large-cavity round: next large-cavity round
+constexpr int kQHuge = 3;   // cavity too large even for the large-cavity workspace: serial path
+
+// Large-cavity rounds: per-candidate workspaces in global memory.
+constexpr uint32_t kBigR = 1024;      // candidates per large-cavity round
+constexpr uint32_t kBigHashN = 4096;  // visited-set slots
+constexpr uint32_t kBigCN = 1024;     // cavity tetrahedra
+constexpr uint32_t kBigFN = 1024;     // boundary facets
+constexpr uint32_t kBigEdgeN = 4096;  // edge-hash slots
+
+// Serial path (one point at a time, one warp): the largest workspaces.
+constexpr uint32_t kHugeHash = 1u << 17;
+constexpr uint32_t kHugeC = 1u << 15;
+constexpr uint32_t kHugeF = 1u << 15;
+constexpr uint32_t kHugeEdge = 1u << 17;
 
 struct BigWS {
   CavWS cav;
   InsWS ins;
 };
 
+// Carves the workspaces of one candidate out of a byte range (global memory).
+__host__ __device__ inline size_t carve(char* base, uint32_t hashn, uint32_t cn, uint32_t fn, uint32_t edgen,
+                                        BigWS* w) {
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    char* r = base ? base + off : nullptr;
+    off += (n + 15) & ~size_t(15);
+    return r;
+  };
+  BigWS x{};
+  x.ins.ekey = (unsigned long long*)take((size_t)edgen * 8);
+  x.ins.nv = (uint4*)take((size_t)fn * 16);
+  x.ins.nn = (uint4*)take((size_t)fn * 16);
+  x.cav.hkey = (uint32_t*)take((size_t)hashn * 4);
+  x.cav.clist = (uint32_t*)take((size_t)cn * 4);
+  x.cav.blist = (uint32_t*)take((size_t)fn * 4);
+  x.ins.eval = (uint32_t*)take((size_t)edgen * 4);
+  x.ins.hslot = (uint32_t*)take((size_t)fn * 3 * 4);
+  x.ins.hold = (uint32_t*)take((size_t)fn * 3 * 4);
+  x.ins.outh = (uint32_t*)take((size_t)fn * 4);
+  x.ins.slot = (uint32_t*)take((size_t)fn * 4);
+  x.ins.vkey = (uint32_t*)take(32 * 4);
+  x.ins.tab = (uint16_t*)take(32 * 32 * 2);
+  x.cav.hval = (uint8_t*)take(hashn);
+  x.ins.ipos = (uint8_t*)take(fn);
+  x.cav.hmask = hashn - 1;
+  x.cav.cmax = cn;
+  x.cav.bmax = fn;
+  x.ins.emask = edgen - 1;
+  if (w) *w = x;
+  return off;
+}
+
+inline size_t big_stride() { return carve(nullptr, kBigHashN, kBigCN, kBigFN, kBigEdgeN, nullptr); }
+
+// Where the candidates of a round come from and where the ones it does not insert go.
+struct RoundIO {
+  const uint32_t* q;  // candidate list; nullptr = the vertex range qbase + idx
+  uint32_t qbase;
+  uint64_t m, L, j;   // segment s of length L offers its point j (Section 3.3 partitions)
+  uint32_t R;         // segments = candidates this round
+  uint32_t* lose_out;
+  int lose_q;
+  uint32_t* big_out;
+  int big_q;
+};
+
 // ------------------------------------------------------------------ kernels of one round
-__global__ void __launch_bounds__(256) k_walk(Ctx c, const uint32_t* __restrict__ q, uint32_t qbase,
-                                              uint64_t m, uint64_t L, uint64_t j, uint32_t R,
-                                              const uint8_t* __restrict__ vflag, uint32_t* cand_p,
-                                              uint32_t* cand_t, uint32_t* cand_status) {
+__global__ void __launch_bounds__(256) k_walk(Ctx c, RoundIO io, const uint8_t* __restrict__ vflag,
+                                              uint32_t* cand_p, uint32_t* cand_t, uint32_t* cand_status) {
   __shared__ unsigned long long s_steps, s_limit;
+  __shared__ unsigned int s_max;
   if (threadIdx.x == 0) {
     s_steps = 0;
     s_limit = 0;
+    s_max = 0;
   }
   __syncthreads();
   uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < R) {
-    uint64_t idx = (uint64_t)s * L + j;
+  if (s < io.R) {
+    uint64_t idx = (uint64_t)s * io.L + io.j;
     uint32_t status = kCandEmpty, p = kNone, t = kNone;
-    if (idx < m) {
-      p = q ? q[idx] : qbase + (uint32_t)idx;
+    if (idx < io.m) {
+      p = io.q ? io.q[idx] : io.qbase + (uint32_t)idx;
       if (vflag[p] == 0) {
         uint32_t anchor = __ldcg(&c.st->anchor);
         Pt P = load_pt(c.pts, p);
+        // hints (Algorithm 1 walks from the previous ball): this point's last stop, then the
+        // segment predecessor's, then the fine and coarse grid cells, then any live tetrahedron
         uint32_t hint = c.point_hint[p];
-        if (hint == kNone) hint = c.cell_hint[cell_of(c, P)];
+        if (hint == kNone && io.j > 0) {
+          uint32_t pp = io.q ? io.q[idx - 1] : io.qbase + (uint32_t)(idx - 1);
+          hint = c.point_hint[pp];
+        }
+        if (hint == kNone) {
+          uint32_t f, g;
+          cells_of(c, P, &f, &g);
+          hint = c.cell_hint[f];
+          if (hint == kNone) hint = c.cell_hint2[g];
+        }
         uint32_t steps = 0;
         status = walk_point(c, P, hint, p * 0x9E3779B1u >> 30, anchor, c.max_walk, &t, &steps);
         atomicAdd(&s_steps, (unsigned long long)steps);
+        atomicMax(&s_max, steps);
         c.point_hint[p] = t;
         if (status == kCandWalkLimit) atomicAdd(&s_limit, 1ull);
       }
@@ -67,16 +140,19 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c, const uint32_t* __restrict_
   if (threadIdx.x == 0) {
     if (s_steps) atomicAdd(&c.st->sum_walk, s_steps);
     if (s_limit) atomicAdd(&c.st->n_walk_limit, s_limit);
+    if (s_max) atomicMax(&c.st->max_walk, (unsigned long long)s_max);
   }
 }
 
+template <bool kBig>
 __global__ void __launch_bounds__(256) k_cavity(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
                                                 const uint32_t* __restrict__ cand_t, uint32_t* cand_status,
-                                                uint32_t* cand_nc, uint32_t* cand_nb, uint32_t* scratch) {
-  __shared__ uint32_t s_hkey[kWarps][kHash];
-  __shared__ uint8_t s_hval[kWarps][kHash];
-  __shared__ uint32_t s_c[kWarps][kCMax];
-  __shared__ uint32_t s_b[kWarps][kFMax];
+                                                uint32_t* cand_nc, uint32_t* cand_nb, uint32_t* scratch,
+                                                char* bigmem, size_t bigstride) {
+  __shared__ uint32_t s_hkey[kBig ? 1 : kWarps][kHash];
+  __shared__ uint8_t s_hval[kBig ? 1 : kWarps][kHash];
+  __shared__ uint32_t s_c[kBig ? 1 : kWarps][kCMax];
+  __shared__ uint32_t s_b[kBig ? 1 : kWarps][kFMax];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t cand = blockIdx.x * kWarps + wid;
   if (cand >= R) return;
@@ -84,10 +160,17 @@ __global__ void __launch_bounds__(256) k_cavity(Ctx c, uint32_t R, const uint32_
   uint32_t p = cand_p[cand];
   Pt P = load_pt(c.pts, p);
   unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
-  CavWS w{s_hkey[wid], s_hval[wid], kHash - 1, s_c[wid], kCMax, s_b[wid], kFMax};
+  CavWS w;
+  if (kBig) {
+    BigWS b;
+    carve(bigmem + (size_t)cand * bigstride, kBigHashN, kBigCN, kBigFN, kBigEdgeN, &b);
+    w = b.cav;
+  } else {
+    w = CavWS{s_hkey[wid], s_hval[wid], kHash - 1, s_c[wid], kCMax, s_b[wid], kFMax};
+  }
   int nc = 0, nb = 0;
   int r = cavity_warp(c, w, cand_t[cand], P, prio, &nc, &nb);
-  if (r == kCandLocated) {
+  if (!kBig && r == kCandLocated) {
     uint32_t* dst = scratch + (size_t)cand * kScratchStride;
     for (int i = lane; i < nc; i += 32) dst[i] = s_c[wid][i];
     for (int i = lane; i < nb; i += 32) dst[kCMax + i] = s_b[wid][i];
@@ -99,19 +182,47 @@ __global__ void __launch_bounds__(256) k_cavity(Ctx c, uint32_t R, const uint32_
   }
 }
 
-__global__ void __launch_bounds__(256) k_insert(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
+// Closes a round (run by the last block of the insert kernel): the allocator consumed the top
+// of the free list, then the bump pointer; slots freed during the round join the free list;
+// the claim stamp advances.
+__device__ void finish_round_block(const Ctx& c) {
+  DevState* st = c.st;
+  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
+  unsigned long long np = __ldcg(&st->pending);
+  __syncthreads();
+  unsigned long long consumed = used < fa ? used : fa;
+  unsigned long long nfa = fa - consumed;
+  if (nfa + np > st->free_capacity) {
+    if (threadIdx.x == 0) raise_error(st, kErrFreeList, 0);
+    np = st->free_capacity - nfa;
+  }
+  for (unsigned long long i = threadIdx.x; i < np; i += blockDim.x) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->bump += used - consumed;
+    st->free_avail = nfa + np;
+    st->alloc_cursor = 0;
+    st->pending = 0;
+    st->stamp += 1;
+    st->blocks_done = 0;
+  }
+}
+
+template <bool kBig>
+__global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_t* __restrict__ cand_p,
                                                 uint32_t* cand_status, const uint32_t* __restrict__ cand_nc,
                                                 const uint32_t* __restrict__ cand_nb,
-                                                const uint32_t* __restrict__ scratch, uint32_t* qnext,
-                                                uint32_t* big) {
-  __shared__ uint4 s_nv[kWarps][kFMax];
-  __shared__ uint4 s_nn[kWarps][kFMax];
-  __shared__ uint32_t s_out[kWarps][kFMax];
-  __shared__ uint32_t s_slot[kWarps][kFMax];
-  __shared__ uint8_t s_ipos[kWarps][kFMax + 4];
-  __shared__ uint32_t s_vkey[kWarps][32];
-  __shared__ uint16_t s_tab[kWarps][32 * 32];
-  __shared__ unsigned int s_nq, s_nbig;
+                                                const uint32_t* __restrict__ scratch, char* bigmem,
+                                                size_t bigstride) {
+  constexpr int W = kBig ? 1 : kWarps;
+  __shared__ uint4 s_nv[W][kFMax];
+  __shared__ uint4 s_nn[W][kFMax];
+  __shared__ uint32_t s_out[W][kFMax];
+  __shared__ uint32_t s_slot[W][kFMax];
+  __shared__ uint8_t s_ipos[W][kFMax + 4];
+  __shared__ uint32_t s_vkey[W][32];
+  __shared__ uint16_t s_tab[W][32 * 32];
+  __shared__ unsigned int s_nq, s_nbig, s_last;
   __shared__ unsigned long long s_qbase, s_bbase;
   __shared__ unsigned long long s_stat[6];  // inserted, conflicts, attempts, cavity, ball, dups
   if (threadIdx.x == 0) {
@@ -123,29 +234,45 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, uint32_t R, const uint32_
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t cand = blockIdx.x * kWarps + wid;
   uint32_t status = kCandEmpty, p = kNone;
-  if (cand < R) {
+  if (cand < io.R) {
     status = cand_status[cand];
     p = cand_p[cand];
   }
   if (status == kCandLocated) {
     unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
-    InsWS w{s_nv[wid], s_nn[wid], s_out[wid], s_slot[wid], s_ipos[wid], s_vkey[wid], s_tab[wid],
-            nullptr, nullptr, nullptr, nullptr, 0};
     int nc = (int)cand_nc[cand], nb = (int)cand_nb[cand];
-    const uint32_t* src = scratch + (size_t)cand * kScratchStride;
-    status = insert_warp(c, w, p, prio, src, nc, src + kCMax, nb, true, __ldcg(&c.st->free_avail),
+    const uint32_t* cl;
+    const uint32_t* bl;
+    InsWS w;
+    if (kBig) {
+      BigWS b;
+      carve(bigmem + (size_t)cand * bigstride, kBigHashN, kBigCN, kBigFN, kBigEdgeN, &b);
+      w = b.ins;
+      cl = b.cav.clist;
+      bl = b.cav.blist;
+    } else {
+      w = InsWS{s_nv[wid], s_nn[wid], s_out[wid], s_slot[wid], s_ipos[wid], s_vkey[wid], s_tab[wid],
+                nullptr, nullptr, nullptr, nullptr, 0};
+      cl = scratch + (size_t)cand * kScratchStride;
+      bl = cl + kCMax;
+    }
+    status = insert_warp(c, w, p, prio, cl, nc, bl, nb, nb <= kFMax, __ldcg(&c.st->free_avail),
                          __ldcg(&c.st->bump), c.st->capacity);
     if (status == kCandInserted && lane == 0) {
       Pt P = load_pt(c.pts, p);
-      c.cell_hint[cell_of(c, P)] = s_slot[wid][0];
-      c.st->anchor = s_slot[wid][0];
+      uint32_t f, g, s0 = w.slot[0];
+      cells_of(c, P, &f, &g);
+      c.cell_hint[f] = s0;
+      c.cell_hint2[g] = s0;
+      c.point_hint[p] = s0;
+      c.st->anchor = s0;
       atomicAdd(&s_stat[0], 1ull);
       atomicAdd(&s_stat[3], (unsigned long long)nc);
       atomicAdd(&s_stat[4], (unsigned long long)nb);
     }
   }
   int qslot = -1, bslot = -1;
-  if (lane == 0 && cand < R && status != kCandEmpty) {
+  if (lane == 0 && cand < io.R && status != kCandEmpty) {
     atomicAdd(&s_stat[2], 1ull);
     if (status == kCandLost) atomicAdd(&s_stat[1], 1ull);
     if (status == kCandDup) atomicAdd(&s_stat[5], 1ull);
@@ -154,23 +281,31 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, uint32_t R, const uint32_
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    s_qbase = s_nq ? atomicAdd(&c.st->qnext, (unsigned long long)s_nq) : 0;
-    s_bbase = s_nbig ? atomicAdd(&c.st->nbig, (unsigned long long)s_nbig) : 0;
+    s_qbase = s_nq ? atomicAdd(&c.st->q[io.lose_q], (unsigned long long)s_nq) : 0;
+    s_bbase = s_nbig ? atomicAdd(&c.st->q[io.big_q], (unsigned long long)s_nbig) : 0;
     if (s_stat[0]) atomicAdd(&c.st->n_inserted, s_stat[0]);
     if (s_stat[1]) atomicAdd(&c.st->n_conflicts, s_stat[1]);
     if (s_stat[2]) atomicAdd(&c.st->n_attempts, s_stat[2]);
     if (s_stat[3]) atomicAdd(&c.st->sum_cavity, s_stat[3]);
     if (s_stat[4]) atomicAdd(&c.st->sum_ball, s_stat[4]);
     if (s_stat[5]) atomicAdd(&c.st->n_dups, s_stat[5]);
+    if (kBig && s_stat[0]) atomicAdd(&c.st->n_big, s_stat[0]);
   }
   __syncthreads();
-  if (qslot >= 0) qnext[s_qbase + qslot] = p;
-  if (bslot >= 0) big[s_bbase + bslot] = p;
+  if (qslot >= 0) io.lose_out[s_qbase + qslot] = p;
+  if (bslot >= 0) io.big_out[s_bbase + bslot] = p;
+  // the last block to finish closes the round
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&c.st->blocks_done, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    finish_round_block(c);
+  }
 }
 
-// Closes a round: the allocator consumed the top of the free list, then the bump pointer;
-// slots freed during the round are appended to the free list; the claim stamp advances.
-// Warp version (one warp runs the kernel); k_finish is the block version.
+// Closes a round run by a single warp (the serial path).
 __device__ void finish_round_warp(const Ctx& c) {
   const int lane = threadIdx.x & 31;
   DevState* st = c.st;
@@ -196,42 +331,23 @@ __device__ void finish_round_warp(const Ctx& c) {
   __syncwarp();
 }
 
-__global__ void k_finish(Ctx c) {
-  // every thread reads the counters before thread 0 rewrites them
-  DevState* st = c.st;
-  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
-  unsigned long long np = __ldcg(&st->pending);
-  __syncthreads();
-  unsigned long long consumed = used < fa ? used : fa;
-  unsigned long long nfa = fa - consumed;
-  if (nfa + np > st->free_capacity) {
-    if (threadIdx.x == 0) raise_error(st, kErrFreeList, 0);
-    np = st->free_capacity - nfa;
-  }
-  for (unsigned long long i = threadIdx.x; i < np; i += blockDim.x) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->bump += used - consumed;
-    st->free_avail = nfa + np;
-    st->alloc_cursor = 0;
-    st->pending = 0;
-    st->stamp += 1;
-  }
-}
-
-// Points whose cavity exceeds the shared-memory path: inserted one at a time by one warp,
-// with global-memory workspaces; nothing else runs concurrently.
-__global__ void k_big(Ctx c, const uint32_t* big, uint32_t nbig, BigWS ws) {
+// Points whose cavity exceeds even the large-cavity workspaces: inserted one at a time by one
+// warp with the largest workspaces; nothing else runs concurrently.
+__global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
   const int lane = threadIdx.x & 31;
-  for (uint32_t k = 0; k < nbig; ++k) {
-    uint32_t p = big[k];
+  for (uint32_t k = 0; k < n; ++k) {
+    uint32_t p = list[k];
     Pt P = load_pt(c.pts, p);
     uint32_t t = kNone, steps = 0;
     int s = 0;
     if (lane == 0) {
       uint32_t anchor = __ldcg(&c.st->anchor);
       uint32_t hint = c.point_hint[p];
-      if (hint == kNone) hint = c.cell_hint[cell_of(c, P)];
+      if (hint == kNone) {
+        uint32_t f, g;
+        cells_of(c, P, &f, &g);
+        hint = c.cell_hint[f];
+      }
       s = walk_point(c, P, hint, 0, anchor, 1u << 22, &t, &steps);
     }
     s = __shfl_sync(kFull, s, 0);
@@ -258,8 +374,12 @@ __global__ void k_big(Ctx c, const uint32_t* big, uint32_t nbig, BigWS ws) {
       return;
     }
     if (lane == 0) {
-      c.cell_hint[cell_of(c, P)] = ws.ins.slot[0];
-      c.st->anchor = ws.ins.slot[0];
+      uint32_t f, g, s0 = ws.ins.slot[0];
+      cells_of(c, P, &f, &g);
+      c.cell_hint[f] = s0;
+      c.cell_hint2[g] = s0;
+      c.point_hint[p] = s0;
+      c.st->anchor = s0;
       c.st->n_inserted += 1;
       c.st->n_big += 1;
       c.st->sum_cavity += nc;
@@ -465,6 +585,7 @@ struct dt_handle {
   uint32_t* pending = nullptr;
   uint64_t cap_free = 0;
   uint32_t* cell_hint = nullptr;
+  uint32_t* cell_hint2 = nullptr;
   int cb = 0, cell_hint_cb = -1;
   double lo[3] = {0, 0, 0}, sc[3] = {0, 0, 0};
   DevState* st = nullptr;
@@ -472,11 +593,12 @@ struct dt_handle {
   uint32_t Rmax = 0;
   uint32_t *cand_p = nullptr, *cand_t = nullptr, *cand_status = nullptr, *cand_nc = nullptr,
            *cand_nb = nullptr, *scratch = nullptr;
-  uint32_t* qnext = nullptr;
-  uint32_t* big = nullptr;
+  uint32_t* queue[4] = {nullptr, nullptr, nullptr, nullptr};  // see kQNext .. kQHuge
   uint64_t cap_q = 0;
-  void* bigmem = nullptr;
-  BigWS bigws{};
+  char* bigmem = nullptr;   // kBigR large-cavity workspaces
+  size_t bigstride = 0;
+  char* hugemem = nullptr;  // the serial path's workspace
+  BigWS hugews{};
   double* bbox_dev = nullptr;
   bool has_mesh = false;
   uint64_t last_n = 0;
@@ -513,6 +635,7 @@ Ctx make_ctx(dt_handle* h) {
   c.freelist = h->freelist;
   c.pending = h->pending;
   c.cell_hint = h->cell_hint;
+  c.cell_hint2 = h->cell_hint2;
   c.point_hint = h->point_hint;
   c.st = h->st;
   for (int k = 0; k < 3; ++k) {
@@ -582,42 +705,18 @@ int reserve_rounds(dt_handle* h, uint64_t qcap) {
         cudaMalloc(&h->cand_nc, R * 4) || cudaMalloc(&h->cand_nb, R * 4) ||
         cudaMalloc(&h->scratch, R * kScratchStride * 4))
       return DT_ENOMEM;
-    size_t bytes = (size_t)kBigHash * 4 + kBigHash + (size_t)kBigC * 4 + (size_t)kBigF * 4 +
-                   (size_t)kBigF * 32 + (size_t)kBigF * 4 * 2 + kBigF + 32 * 4 + 32 * 32 * 2 +
-                   (size_t)kBigEdge * 8 + (size_t)kBigEdge * 4 + (size_t)kBigF * 3 * 4 * 2 + 1024;
-    if (cudaMalloc(&h->bigmem, bytes)) return DT_ENOMEM;
-    char* b = (char*)h->bigmem;
-    auto take = [&](size_t n) {
-      char* r = b;
-      b += (n + 15) & ~size_t(15);
-      return r;
-    };
-    BigWS& w = h->bigws;
-    w.ins.ekey = (unsigned long long*)take((size_t)kBigEdge * 8);
-    w.ins.nv = (uint4*)take((size_t)kBigF * 16);
-    w.ins.nn = (uint4*)take((size_t)kBigF * 16);
-    w.cav.hkey = (uint32_t*)take((size_t)kBigHash * 4);
-    w.cav.clist = (uint32_t*)take((size_t)kBigC * 4);
-    w.cav.blist = (uint32_t*)take((size_t)kBigF * 4);
-    w.ins.eval = (uint32_t*)take((size_t)kBigEdge * 4);
-    w.ins.hslot = (uint32_t*)take((size_t)kBigF * 3 * 4);
-    w.ins.hold = (uint32_t*)take((size_t)kBigF * 3 * 4);
-    w.ins.outh = (uint32_t*)take((size_t)kBigF * 4);
-    w.ins.slot = (uint32_t*)take((size_t)kBigF * 4);
-    w.ins.vkey = (uint32_t*)take(32 * 4);
-    w.ins.tab = (uint16_t*)take(32 * 32 * 2);
-    w.cav.hval = (uint8_t*)take(kBigHash);
-    w.ins.ipos = (uint8_t*)take(kBigF);
-    w.cav.hmask = kBigHash - 1;
-    w.cav.cmax = kBigC;
-    w.cav.bmax = kBigF;
-    w.ins.emask = kBigEdge - 1;
+    h->bigstride = big_stride();
+    if (cudaMalloc(&h->bigmem, h->bigstride * kBigR)) return DT_ENOMEM;
+    size_t huge = carve(nullptr, kHugeHash, kHugeC, kHugeF, kHugeEdge, nullptr);
+    if (cudaMalloc(&h->hugemem, huge)) return DT_ENOMEM;
+    carve(h->hugemem, kHugeHash, kHugeC, kHugeF, kHugeEdge, &h->hugews);
   }
   if (qcap > h->cap_q) {
-    cudaFree(h->qnext);
-    cudaFree(h->big);
-    h->qnext = h->big = nullptr;
-    if (cudaMalloc(&h->qnext, qcap * 4) || cudaMalloc(&h->big, qcap * 4)) return DT_ENOMEM;
+    for (auto& qb : h->queue) {
+      cudaFree(qb);
+      qb = nullptr;
+      if (cudaMalloc(&qb, qcap * 4)) return DT_ENOMEM;
+    }
     h->cap_q = qcap;
   }
   return DT_OK;
@@ -630,6 +729,79 @@ uint32_t choose_segments(dt_handle* h, uint64_t mesh_vertices, uint64_t m) {
   R = std::min<uint64_t>(R, h->Rmax);
   R = std::min<uint64_t>(R, m);
   return (uint32_t)std::max<uint64_t>(R, 1);
+}
+
+// One concurrent insertion round: walk, cavity + claims, ball (+ closing the round).
+void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, bool big, uint64_t j_prof) {
+  const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0 && !big;
+  cudaStream_t s = h->stream;
+  uint32_t R = io.R;
+  if (prof) cudaEventRecord(h->prof_events[6 * j_prof], s);
+  k_walk<<<(R + 255) / 256, 256, 0, s>>>(c, io, h->vflag, h->cand_p, h->cand_t, h->cand_status);
+  ++g_kernel_launches;
+  if (prof) {
+    cudaEventRecord(h->prof_events[6 * j_prof + 1], s);
+    cudaEventRecord(h->prof_events[6 * j_prof + 2], s);
+  }
+  unsigned blocks = (R + kWarps - 1) / kWarps;
+  if (big)
+    k_cavity<true><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
+                                           h->scratch, h->bigmem, h->bigstride);
+  else
+    k_cavity<false><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
+                                            h->scratch, h->bigmem, h->bigstride);
+  ++g_kernel_launches;
+  if (prof) {
+    cudaEventRecord(h->prof_events[6 * j_prof + 3], s);
+    cudaEventRecord(h->prof_events[6 * j_prof + 4], s);
+  }
+  if (big)
+    k_insert<true><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
+                                           h->bigmem, h->bigstride);
+  else
+    k_insert<false><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb,
+                                            h->scratch, h->bigmem, h->bigstride);
+  ++g_kernel_launches;
+  if (prof) cudaEventRecord(h->prof_events[6 * j_prof + 5], s);
+  h->stats.n_rounds++;
+}
+
+int set_queue_lengths(dt_handle* h, std::initializer_list<int> which) {
+  unsigned long long zero = 0;
+  for (int q : which)
+    if (cudaMemcpyAsync(&h->st->q[q], &zero, 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return DT_ECUDA;
+  return DT_OK;
+}
+
+// Large cavities of a pass: rounds of up to kBigR candidates with global-memory workspaces
+// (losers retry in the next such round), then the serial path for any larger ones.
+int run_big(dt_handle* h, const Ctx& c) {
+  uint64_t nbig = h->st_host->q[kQBig];
+  int guard = 0;
+  while (nbig > 0) {
+    if (++guard > 100000) return DT_ELIMIT;
+    int rc = set_queue_lengths(h, {kQBig2});
+    if (rc != DT_OK) return rc;
+    uint32_t R = (uint32_t)std::min<uint64_t>(nbig, kBigR);
+    uint64_t L = (nbig + R - 1) / R;
+    for (uint64_t j = 0; j < L; ++j) {
+      RoundIO io{h->queue[kQBig], 0, nbig, L, j, R, h->queue[kQBig2], kQBig2, h->queue[kQHuge], kQHuge};
+      launch_round(h, c, io, true, 0);
+    }
+    if ((rc = sync_state(h)) != DT_OK) return rc;
+    nbig = h->st_host->q[kQBig2];
+    std::swap(h->queue[kQBig], h->queue[kQBig2]);
+  }
+  uint64_t nhuge = h->st_host->q[kQHuge];
+  if (nhuge) {
+    Ctx cc = c;
+    cc.coherent = 1;
+    k_huge<<<1, 32, 0, h->stream>>>(cc, h->queue[kQHuge], (uint32_t)nhuge, h->hugews);
+    ++g_kernel_launches;
+    int rc = sync_state(h);
+    if (rc != DT_OK) return rc;
+  }
+  return DT_OK;
 }
 
 // Inserts the vertices [vbegin, vend) (one BRIO round, Moore order) by passes of concurrent
@@ -647,8 +819,8 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend) {
     uint64_t before = h->st_host->n_inserted + h->st_host->n_dups;
     uint32_t R = choose_segments(h, mesh, m);
     uint64_t L = (m + R - 1) / R;
-    unsigned long long zero2[2] = {0, 0};
-    cudaMemcpyAsync(&h->st->qnext, zero2, 16, cudaMemcpyHostToDevice, h->stream);
+    int rc = set_queue_lengths(h, {kQNext, kQBig, kQHuge});
+    if (rc != DT_OK) return rc;
     const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0;
     if (prof) {
       while (h->prof_events.size() < 6 * L) {
@@ -658,28 +830,12 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend) {
       }
     }
     for (uint64_t j = 0; j < L; ++j) {
-      if (prof) cudaEventRecord(h->prof_events[6 * j], h->stream);
-      k_walk<<<(R + 255) / 256, 256, 0, h->stream>>>(c, q, qbase, m, L, j, R, h->vflag, h->cand_p, h->cand_t,
-                                                      h->cand_status);
-      ++g_kernel_launches;
-      if (prof) cudaEventRecord(h->prof_events[6 * j + 1], h->stream);
-      if (prof) cudaEventRecord(h->prof_events[6 * j + 2], h->stream);
-      k_cavity<<<(R + kWarps - 1) / kWarps, 256, 0, h->stream>>>(c, R, h->cand_p, h->cand_t, h->cand_status,
-                                                                  h->cand_nc, h->cand_nb, h->scratch);
-      ++g_kernel_launches;
-      if (prof) cudaEventRecord(h->prof_events[6 * j + 3], h->stream);
-      if (prof) cudaEventRecord(h->prof_events[6 * j + 4], h->stream);
-      k_insert<<<(R + kWarps - 1) / kWarps, 256, 0, h->stream>>>(c, R, h->cand_p, h->cand_status, h->cand_nc,
-                                                                  h->cand_nb, h->scratch, h->qnext, h->big);
-      ++g_kernel_launches;
-      if (prof) cudaEventRecord(h->prof_events[6 * j + 5], h->stream);
-      k_finish<<<1, 256, 0, h->stream>>>(c);
-      ++g_kernel_launches;
-      h->stats.n_rounds++;
+      RoundIO io{q, qbase, m, L, j, R, h->queue[kQNext], kQNext, h->queue[kQBig], kQBig};
+      launch_round(h, c, io, false, j);
     }
     h->stats.n_passes++;
-    int rc = sync_state(h);
-    if (rc != DT_OK) return rc;
+    if ((rc = sync_state(h)) != DT_OK) return rc;
+    if (cudaGetLastError() != cudaSuccess) return DT_ECUDA;
     if (prof) {
       for (uint64_t j = 0; j < L; ++j) {
         float a = 0, b = 0, cc = 0;
@@ -692,24 +848,16 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend) {
         h->stats.n_profiled++;
       }
     }
-    if (cudaGetLastError() != cudaSuccess) return DT_ECUDA;
-    uint64_t nbig = h->st_host->nbig, nq = h->st_host->qnext;
-    if (nbig) {
-      Ctx cb = c;
-      cb.coherent = 1;
-      k_big<<<1, 32, 0, h->stream>>>(cb, h->big, (uint32_t)nbig, h->bigws);
-      ++g_kernel_launches;
-      rc = sync_state(h);
-      if (rc != DT_OK) return rc;
-    }
+    uint64_t nq = h->st_host->q[kQNext];
+    if ((rc = run_big(h, c)) != DT_OK) return rc;
     if (h->stats.n_rounds > max_rounds) return DT_ELIMIT;
     if (nq == 0) break;
     // a pass that inserted nothing three times in a row is a bug, not a schedule
     stalled = (h->st_host->n_inserted + h->st_host->n_dups == before) ? stalled + 1 : 0;
     if (stalled >= 3) return DT_ELIMIT;
     // re-partition the failed points: transformed keys, then sort (Section 3.3)
-    transformed_keys(h->pts, h->qnext, nq, h->bbox_dev, h->cfg.seed + 0x51ED2701ull * (pass + 1) + vbegin,
-                     h->ows.k0, h->ows.v0, h->stream);
+    transformed_keys(h->pts, h->queue[kQNext], nq, h->bbox_dev,
+                     h->cfg.seed + 0x51ED2701ull * (pass + 1) + vbegin, h->ows.k0, h->ows.v0, h->stream);
     bool alt = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, nq, 64, h->ows.hist, h->stream);
     q = alt ? h->ows.v1 : h->ows.v0;
     m = nq;
@@ -748,13 +896,17 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
       double ext = bb[3 + k] - bb[k];
       h->sc[k] = ext > 0 ? (double)(1u << cb) / ext : 0.0;
     }
+    int cbc = cb > 3 ? cb - 3 : 1;
     if (h->cell_hint_cb != cb) {
       cudaFree(h->cell_hint);
-      h->cell_hint = nullptr;
+      cudaFree(h->cell_hint2);
+      h->cell_hint = h->cell_hint2 = nullptr;
       if (cudaMalloc(&h->cell_hint, (size_t)4 << (3 * cb)) != cudaSuccess) return DT_ENOMEM;
+      if (cudaMalloc(&h->cell_hint2, (size_t)4 << (3 * cbc)) != cudaSuccess) return DT_ENOMEM;
       h->cell_hint_cb = cb;
     }
     cudaMemsetAsync(h->cell_hint, 0xFF, (size_t)4 << (3 * cb), s);
+    cudaMemsetAsync(h->cell_hint2, 0xFF, (size_t)4 << (3 * cbc), s);
     DevState z{};
     z.stamp = h->next_stamp;
     z.capacity = h->cap_tets;
@@ -806,6 +958,7 @@ void fill_stats(dt_handle* h, dt_stats* o) {
   o->n_sos = d.n_sos;
   o->reserved[0] = d.n_walk_limit;
   o->reserved[1] = d.free_avail;
+  o->reserved[2] = d.max_walk;
 }
 
 }  // namespace
@@ -1005,6 +1158,7 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->freelist);
   cudaFree(h->pending);
   cudaFree(h->cell_hint);
+  cudaFree(h->cell_hint2);
   cudaFree(h->st);
   if (h->st_host) cudaFreeHost(h->st_host);
   cudaFree(h->cand_p);
@@ -1013,9 +1167,9 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->cand_nc);
   cudaFree(h->cand_nb);
   cudaFree(h->scratch);
-  cudaFree(h->qnext);
-  cudaFree(h->big);
+  for (auto& qb : h->queue) cudaFree(qb);
   cudaFree(h->bigmem);
+  cudaFree(h->hugemem);
   cudaFree(h->bbox_dev);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);

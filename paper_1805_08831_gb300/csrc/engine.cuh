@@ -43,8 +43,9 @@ struct Ctx {
   const Pt* pts;  // .w = input index (the perturbation order)
   uint32_t* freelist;
   uint32_t* pending;
-  uint32_t* cell_hint;
-  uint32_t* point_hint;
+  uint32_t* cell_hint;    // fine grid: a recent tetrahedron per cell
+  uint32_t* cell_hint2;   // coarse grid (8 x 8 x 8 fine cells per coarse cell)
+  uint32_t* point_hint;   // per vertex: where its last walk ended / its ball
   DevState* st;
   double lo[3], sc[3];
   int cb;  // bits per axis of the hint grid
@@ -110,7 +111,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-__device__ __forceinline__ uint32_t cell_of(const Ctx& c, Pt P) {
+// Fine and coarse hint-grid cells of P.
+__device__ __forceinline__ void cells_of(const Ctx& c, Pt P, uint32_t* fine, uint32_t* coarse) {
   double x[3] = {P.x, P.y, P.z};
   double lim = (double)((1u << c.cb) - 1u);
   uint32_t q[3];
@@ -119,7 +121,9 @@ __device__ __forceinline__ uint32_t cell_of(const Ctx& c, Pt P) {
     f = f < 0.0 ? 0.0 : (f > lim ? lim : f);
     q[k] = (uint32_t)f;
   }
-  return (q[2] << (2 * c.cb)) | (q[1] << c.cb) | q[0];
+  *fine = (q[2] << (2 * c.cb)) | (q[1] << c.cb) | q[0];
+  int cc = c.cb > 3 ? c.cb - 3 : 1, sh = c.cb - cc;
+  *coarse = ((q[2] >> sh) << (2 * cc)) | ((q[1] >> sh) << cc) | (q[0] >> sh);
 }
 
 // Positions (a, b, c) such that (p, w[a], w[b], w[c]) is an even permutation of a tetrahedron

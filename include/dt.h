@@ -147,6 +147,29 @@ void dt_destroy(dt_handle* h);
 /* Static description of an error code. */
 const char* dt_strerror(int code);
 
+/* Largest point count dt_order_noalloc accepts. */
+#define DT_NOALLOC_MAX_POINTS 262144u
+
+/* The spatial order of dt_get_order (Moore keys, BRIO rounds, insertion permutation) computed
+ * without allocating any device memory. The paper has no counterpart; this entry point exists
+ * for callers that cannot call cudaMalloc: code that runs while a CUDA stream is being captured
+ * into a graph, hosts whose device memory is all owned by another allocator, and latency-bound
+ * callers that cannot pay cudaMalloc's implicit device synchronisation.
+ *  - xyz_dev: [n, 3] float64 row-major (device); n <= DT_NOALLOC_MAX_POINTS, else DT_EINVAL.
+ *  - keys_dev [n] uint64, perm_dev [n] uint32, rounds_dev [n] uint8: device outputs, owned by
+ *    the caller; same values as dt_get_order after dt_insert of the same points and seed.
+ *  - stream: cudaStream_t (NULL = default stream); the call returns after the stream is done.
+ * The working memory is one file-scope device array of about 6.6 MB that every device loading
+ * the library holds until the process exits. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture begins. All calls share the array and each leaves its contents
+ * behind (the parts that must start at zero are cleared at the start of every call): calls
+ * that overlap on the GPU, from several host threads or streams, race and must be serialised
+ * by the caller. Errors: DT_EINVAL (bad pointer, size over the limit, non-finite or
+ * |x| > 1e30 coordinate), DT_ECUDA. */
+int dt_order_noalloc(const double* xyz_dev, uint64_t n, uint64_t seed, uint64_t* keys_dev, uint32_t* perm_dev,
+                     uint8_t* rounds_dev, void* stream);
+
 /* Exact predicate signs on the device, for testing the predicates in isolation (Section 2.4):
  * for each of n tuples, kind 0 = orient3d(a,b,c,d) (4 points), 1 = insphere(a,b,c,d,e) (5 points,
  * unperturbed), 2 = perturbed insphere with ids_dev giving the 5 point identities.

@@ -101,6 +101,7 @@ def lib():
         L.dt_strerror.argtypes = [ctypes.c_int]
         L.dt_strerror.restype = ctypes.c_char_p
         L.dt_eval_predicates.argtypes = [ctypes.c_int, p, p, p, u64, p]
+        L.dt_order_noalloc.argtypes = [p, u64, u64, p, p, p, p]
         for name in exported_names():
             getattr(L, name)
         _lib = L

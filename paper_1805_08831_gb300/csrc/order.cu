@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -461,9 +462,9 @@ void order_ws_free(OrderWS& ws) {
   ws = OrderWS();
 }
 
-int order_points(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cudaStream_t s) {
+// S1..S4 on a workspace that already holds room for n points (allocates nothing).
+int order_points_ws(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cudaStream_t s) {
   if (n == 0) return DT_OK;
-  if (order_ws_reserve(ws, n) != cudaSuccess) return DT_ENOMEM;
   cudaMemsetAsync(ws.bad, 0, 4, s);
   cudaMemsetAsync(ws.dup, 0, n, s);
   k_bbox_partial<<<kBoxBlocks, kBoxThreads, 0, s>>>(xyz, n, ws.partial, ws.bad);
@@ -499,6 +500,12 @@ int order_points(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cuda
   return DT_OK;
 }
 
+int order_points(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cudaStream_t s) {
+  if (n == 0) return DT_OK;
+  if (order_ws_reserve(ws, n) != cudaSuccess) return DT_ENOMEM;
+  return order_points_ws(xyz, n, seed, ws, s);
+}
+
 void transformed_keys(const Pt* pts, const uint32_t* ids, uint64_t m, const double* bbox,
                       uint64_t seed, uint64_t* keys_out, uint32_t* vals_out, cudaStream_t s) {
   if (m == 0) return;
@@ -507,3 +514,72 @@ void transformed_keys(const Pt* pts, const uint32_t* ids, uint64_t m, const doub
 }
 
 }  // namespace dtg
+
+// ------------------------------------------------------------------ ordering without allocation
+// Scratch of dt_order_noalloc: a file-scope device array, present on every device that loads
+// the library, reused by every call (see include/dt.h).
+namespace dtg {
+namespace {
+
+constexpr uint64_t kNoAllocMax = DT_NOALLOC_MAX_POINTS;
+constexpr uint64_t kNoAllocHist = (256ull * ((kNoAllocMax + 4095) / 4096)) + 1024;
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kOffK0 = 0;
+constexpr size_t kOffK1 = kOffK0 + align256(kNoAllocMax * 8);
+constexpr size_t kOffV0 = kOffK1 + align256(kNoAllocMax * 8);
+constexpr size_t kOffV1 = kOffV0 + align256(kNoAllocMax * 4);
+constexpr size_t kOffDup = kOffV1 + align256(kNoAllocMax * 4);
+constexpr size_t kOffHist = kOffDup + align256(kNoAllocMax);
+constexpr size_t kOffBox = kOffHist + align256(kNoAllocHist * 4);
+constexpr size_t kOffPart = kOffBox + align256(6 * 8);
+constexpr size_t kOffBad = kOffPart + align256(kBoxBlocks * 6 * 8);
+constexpr size_t kNoAllocBytes = kOffBad + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[1024] = {};
+
+// Host address of the device array on the current device, looked up once per device.
+int noalloc_scratch(char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 1024) return DT_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DT_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<char*>(g_noalloc_ptr[dev]);
+  return DT_OK;
+}
+
+}  // namespace
+}  // namespace dtg
+
+extern "C" int dt_order_noalloc(const double* xyz_dev, uint64_t n, uint64_t seed, uint64_t* keys_dev,
+                                uint32_t* perm_dev, uint8_t* rounds_dev, void* stream) {
+  using namespace dtg;
+  if (n > kNoAllocMax) return DT_EINVAL;
+  if (n > 0 && (!xyz_dev || !keys_dev || !perm_dev || !rounds_dev)) return DT_EINVAL;
+  if (n == 0) return DT_OK;
+  char* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc != DT_OK) return rc;
+  OrderWS ws;
+  ws.cap = kNoAllocMax;
+  ws.keys = keys_dev;
+  ws.perm = perm_dev;
+  ws.rounds = rounds_dev;
+  ws.k0 = reinterpret_cast<uint64_t*>(base + kOffK0);
+  ws.k1 = reinterpret_cast<uint64_t*>(base + kOffK1);
+  ws.v0 = reinterpret_cast<uint32_t*>(base + kOffV0);
+  ws.v1 = reinterpret_cast<uint32_t*>(base + kOffV1);
+  ws.dup = reinterpret_cast<uint8_t*>(base + kOffDup);
+  ws.hist = reinterpret_cast<uint32_t*>(base + kOffHist);
+  ws.hist_cap = kNoAllocHist;
+  ws.bbox = reinterpret_cast<double*>(base + kOffBox);
+  ws.partial = reinterpret_cast<double*>(base + kOffPart);
+  ws.bad = reinterpret_cast<unsigned int*>(base + kOffBad);
+  return order_points_ws(xyz_dev, n, seed, ws, static_cast<cudaStream_t>(stream));
+}

@@ -159,7 +159,7 @@ const char* dt_strerror(int code);
  *  - keys_dev [n] uint64, perm_dev [n] uint32, rounds_dev [n] uint8: device outputs, owned by
  *    the caller; same values as dt_get_order after dt_insert of the same points and seed.
  *  - stream: cudaStream_t (NULL = default stream); the call returns after the stream is done.
- * The working memory is one file-scope device array of about 6.6 MB that every device loading
+ * The working memory is one file-scope device array of about 7.7 MB that every device loading
  * the library holds until the process exits. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current, so make that first call
  * before any stream capture begins. All calls share the array and each leaves its contents
@@ -172,7 +172,9 @@ int dt_order_noalloc(const double* xyz_dev, uint64_t n, uint64_t seed, uint64_t*
 
 /* Exact predicate signs on the device, for testing the predicates in isolation (Section 2.4):
  * for each of n tuples, kind 0 = orient3d(a,b,c,d) (4 points), 1 = insphere(a,b,c,d,e) (5 points,
- * unperturbed), 2 = perturbed insphere with ids_dev giving the 5 point identities.
+ * unperturbed), 2 = perturbed insphere with ids_dev giving the 5 point identities; kinds 3
+ * (orient3d) and 4 (perturbed insphere) run the insertion kernels' full pipeline: the FP32
+ * stage on a double-float copy of the points, then the FP64 filter, then exact arithmetic.
  * pts_dev: [n, 5, 3] float64 (unused slots ignored); ids_dev: [n, 5] int64 (kind 2 only, else
  * NULL); out_dev: [n] int8 signs. */
 int dt_eval_predicates(int kind, const double* pts_dev, const int64_t* ids_dev, int8_t* out_dev,

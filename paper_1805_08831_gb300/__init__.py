@@ -165,6 +165,12 @@ class Triangulation:
         """Starts over with an empty triangulation, keeping the device memory."""
         _check(lib().dt_clear(self._h), "dt_clear")
 
+    def _check_dev(self, rc, what):
+        if rc != DT_OK:
+            st = Stats()
+            lib().dt_get_stats(self._h, ctypes.byref(st))
+            raise DTError(rc, f"{what} (device error {st.device_error}, info {st.device_error_info:#x})")
+
     def insert(self, xyz):
         """Inserts a CUDA float64 tensor [n, 3] (device pointer path)."""
         torch = _torch()
@@ -173,15 +179,15 @@ class Triangulation:
         xyz = xyz.contiguous()
         if xyz.dim() != 2 or xyz.shape[1] != 3:
             raise ValueError("xyz must be [n, 3]")
-        _check(lib().dt_insert(self._h, ctypes.c_void_p(xyz.data_ptr()), xyz.shape[0]), "dt_insert")
+        self._check_dev(lib().dt_insert(self._h, ctypes.c_void_p(xyz.data_ptr()), xyz.shape[0]), "dt_insert")
 
     def insert_host(self, xyz):
         """Inserts host float64 points [n, 3] (copied to the device inside the call)."""
         a = np.ascontiguousarray(xyz, dtype=np.float64)
         if a.ndim != 2 or a.shape[1] != 3:
             raise ValueError("xyz must be [n, 3]")
-        _check(lib().dt_insert_host(self._h, a.ctypes.data_as(ctypes.c_void_p), a.shape[0]),
-               "dt_insert_host")
+        self._check_dev(lib().dt_insert_host(self._h, a.ctypes.data_as(ctypes.c_void_p), a.shape[0]),
+                        "dt_insert_host")
 
     def num_tets(self) -> int:
         n = ctypes.c_uint64()

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c, RoundIO io, const uint8_t* 
       p = io.q ? io.q[idx] : io.qbase + (uint32_t)idx;
       if (vflag[p] == 0) {
         uint32_t anchor = __ldcg(&c.st->anchor);
-        Pt P = load_pt(c.pts, p);
+        PtF FP = load_ptf(c.ptf, p);
         // hints (Algorithm 1 walks from the previous ball): this point's last stop, then the
         // segment predecessor's, then the fine and coarse grid cells, then any live tetrahedron
         uint32_t hint = c.point_hint[p];
@@ -120,12 +120,12 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c, RoundIO io, const uint8_t* 
         }
         if (hint == kNone) {
           uint32_t f, g;
-          cells_of(c, P, &f, &g);
+          cells_of(c, FP, &f, &g);
           hint = c.cell_hint[f];
           if (hint == kNone) hint = c.cell_hint2[g];
         }
         uint32_t steps = 0;
-        status = walk_point(c, P, hint, p * 0x9E3779B1u >> 30, anchor, c.max_walk, &t, &steps);
+        status = walk_point(c, p, FP, hint, p * 0x9E3779B1u >> 30, anchor, c.max_walk, &t, &steps);
         atomicAdd(&s_steps, (unsigned long long)steps);
         atomicMax(&s_max, steps);
         c.point_hint[p] = t;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_cavity(Ctx c, uint32_t R, const uint32_
   if (cand >= R) return;
   if (cand_status[cand] != kCandLocated) return;
   uint32_t p = cand_p[cand];
-  Pt P = load_pt(c.pts, p);
+  PtF FP = load_ptf(c.ptf, p);
   unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
   CavWS w;
   if (kBig) {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_cavity(Ctx c, uint32_t R, const uint32_
     w = CavWS{s_hkey[wid], s_hval[wid], kHash - 1, s_c[wid], kCMax, s_b[wid], kFMax};
   }
   int nc = 0, nb = 0;
-  int r = cavity_warp(c, w, cand_t[cand], P, prio, &nc, &nb);
+  int r = cavity_warp(c, w, cand_t[cand], p, FP, prio, &nc, &nb);
   if (!kBig && r == kCandLocated) {
     uint32_t* dst = scratch + (size_t)cand * kScratchStride;
     for (int i = lane; i < nc; i += 32) dst[i] = s_c[wid][i];
@@ -205,7 +205,9 @@ __device__ void finish_round_block(const Ctx& c) {
     st->pending = 0;
     st->stamp += 1;
     st->blocks_done = 0;
+    __threadfence();
   }
+  __syncthreads();
 }
 
 template <bool kBig>
@@ -259,9 +261,9 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
     status = insert_warp(c, w, p, prio, cl, nc, bl, nb, nb <= kFMax, __ldcg(&c.st->free_avail),
                          __ldcg(&c.st->bump), c.st->capacity);
     if (status == kCandInserted && lane == 0) {
-      Pt P = load_pt(c.pts, p);
+      PtF FP = load_ptf(c.ptf, p);
       uint32_t f, g, s0 = w.slot[0];
-      cells_of(c, P, &f, &g);
+      cells_of(c, FP, &f, &g);
       c.cell_hint[f] = s0;
       c.cell_hint2[g] = s0;
       c.point_hint[p] = s0;
@@ -337,7 +339,7 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
   const int lane = threadIdx.x & 31;
   for (uint32_t k = 0; k < n; ++k) {
     uint32_t p = list[k];
-    Pt P = load_pt(c.pts, p);
+    PtF FP = load_ptf(c.ptf, p);
     uint32_t t = kNone, steps = 0;
     int s = 0;
     if (lane == 0) {
@@ -345,10 +347,10 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
       uint32_t hint = c.point_hint[p];
       if (hint == kNone) {
         uint32_t f, g;
-        cells_of(c, P, &f, &g);
+        cells_of(c, FP, &f, &g);
         hint = c.cell_hint[f];
       }
-      s = walk_point(c, P, hint, 0, anchor, 1u << 22, &t, &steps);
+      s = walk_point(c, p, FP, hint, 0, anchor, 1u << 22, &t, &steps);
     }
     s = __shfl_sync(kFull, s, 0);
     t = __shfl_sync(kFull, t, 0);
@@ -362,7 +364,7 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
     }
     unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
     int nc = 0, nb = 0;
-    int r = cavity_warp(c, ws.cav, t, P, prio, &nc, &nb);
+    int r = cavity_warp(c, ws.cav, t, p, FP, prio, &nc, &nb);
     if (r != kCandLocated) {
       if (lane == 0) raise_error(c.st, kErrBigCavity, p);
       return;
@@ -375,7 +377,7 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
     }
     if (lane == 0) {
       uint32_t f, g, s0 = ws.ins.slot[0];
-      cells_of(c, P, &f, &g);
+      cells_of(c, FP, &f, &g);
       c.cell_hint[f] = s0;
       c.cell_hint2[g] = s0;
       c.point_hint[p] = s0;
@@ -388,6 +390,180 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
     __threadfence();
     __syncwarp();
     finish_round_warp(c);
+  }
+}
+
+
+// ------------------------------------------------------------------ one-block engine
+// The first insertions of a cloud (a few thousand points into a mesh that starts with one
+// tetrahedron) offer little parallelism and many conflicts: here one thread block runs whole
+// passes itself, with block barriers in place of kernel boundaries between the walk, cavity
+// and ball phases of a round (up to kCtaWarps concurrent insertions). Large cavities go to the
+// large-cavity queue for the grid path.
+constexpr int kCtaWarps = 16;
+
+struct CtaWarpSmem {
+  uint4 nv[kFMax];
+  uint4 nn[kFMax];
+  uint32_t hkey[kHash];
+  uint32_t clist[kCMax];
+  uint32_t blist[kFMax];
+  uint32_t outh[kFMax];
+  uint32_t slot[kFMax];
+  uint32_t vkey[32];
+  uint16_t tab[32 * 32];
+  uint8_t hval[kHash];
+  uint8_t ipos[kFMax + 4];
+};
+
+__global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, uint32_t vbegin, uint32_t m0,
+                                                               const uint8_t* __restrict__ vflag,
+                                                               uint32_t* list_a, uint32_t* list_b,
+                                                               uint32_t* big_out, float alpha,
+                                                               uint32_t max_passes) {
+  extern __shared__ __align__(16) unsigned char cta_smem[];
+  CtaWarpSmem* ws = reinterpret_cast<CtaWarpSmem*>(cta_smem);
+  __shared__ uint32_t s_p[kCtaWarps], s_t[kCtaWarps], s_st[kCtaWarps], s_nc[kCtaWarps], s_nb[kCtaWarps];
+  __shared__ unsigned int s_nout, s_R, s_err;
+  __shared__ unsigned long long s_L, s_N0;
+  __shared__ unsigned long long s_stat[6];  // inserted, conflicts, attempts, cavity, ball, walk
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const uint32_t* q = nullptr;
+  uint32_t* out = list_a;
+  uint64_t m = m0;
+  if (tid < 6) s_stat[tid] = 0;
+  if (tid == 0) s_N0 = __ldcg(&c.st->n_inserted);
+  __syncthreads();
+  for (uint32_t pass = 0; m > 0 && pass < max_passes; ++pass) {
+    if (tid == 0) {
+      double N = (double)(s_N0 + s_stat[0]);
+      uint64_t R = (uint64_t)fmax(1.0, alpha * N);
+      R = R > kCtaWarps ? kCtaWarps : R;
+      R = R > m ? m : R;
+      s_R = (unsigned)R;
+      s_L = (m + R - 1) / R;
+      s_nout = 0;
+      s_err = __ldcg(&c.st->error);
+    }
+    __syncthreads();
+    if (s_err) break;
+    const uint32_t R = s_R;
+    const uint64_t L = s_L;
+    for (uint64_t j = 0; j < L; ++j) {
+      // walk: one thread per candidate
+      if (tid < (int)R) {
+        uint64_t idx = (uint64_t)tid * L + j;
+        uint32_t status = kCandEmpty, p = kNone, t = kNone;
+        if (idx < m) {
+          p = q ? q[idx] : vbegin + (uint32_t)idx;
+          if (vflag[p] == 0) {
+            PtF FP = load_ptf(c.ptf, p);
+            uint32_t hint = c.point_hint[p];
+            if (hint == kNone && j > 0) hint = c.point_hint[q ? q[idx - 1] : vbegin + (uint32_t)(idx - 1)];
+            if (hint == kNone) {
+              uint32_t f, g;
+              cells_of(c, FP, &f, &g);
+              hint = c.cell_hint[f];
+              if (hint == kNone) hint = c.cell_hint2[g];
+            }
+            uint32_t steps = 0;
+            status = walk_point(c, p, FP, hint, p * 0x9E3779B1u >> 30, __ldcg(&c.st->anchor), c.max_walk, &t, &steps);
+            atomicAdd(&s_stat[5], (unsigned long long)steps);
+            c.point_hint[p] = t;
+          }
+        }
+        s_p[tid] = p;
+        s_t[tid] = t;
+        s_st[tid] = status;
+      }
+      __syncthreads();
+      // cavity: one warp per candidate
+      if (wid < (int)R && s_st[wid] == kCandLocated) {
+        uint32_t p = s_p[wid];
+        unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+        CtaWarpSmem& w = ws[wid];
+        CavWS cw{w.hkey, w.hval, kHash - 1, w.clist, kCMax, w.blist, kFMax};
+        int nc = 0, nb = 0;
+        int r = cavity_warp(c, cw, s_t[wid], p, load_ptf(c.ptf, p), prio, &nc, &nb);
+        if (lane == 0) {
+          s_st[wid] = (uint32_t)r;
+          s_nc[wid] = (uint32_t)nc;
+          s_nb[wid] = (uint32_t)nb;
+        }
+      }
+      __syncthreads();
+      // ball: the same warp, from its shared-memory cavity
+      if (wid < (int)R && s_st[wid] == kCandLocated) {
+        uint32_t p = s_p[wid];
+        unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+        CtaWarpSmem& w = ws[wid];
+        InsWS iw{w.nv, w.nn, w.outh, w.slot, w.ipos, w.vkey, w.tab, nullptr, nullptr, nullptr, nullptr, 0};
+        int nc = (int)s_nc[wid], nb = (int)s_nb[wid];
+        int r = insert_warp(c, iw, p, prio, w.clist, nc, w.blist, nb, true, __ldcg(&c.st->free_avail),
+                            __ldcg(&c.st->bump), c.st->capacity);
+        if (lane == 0) {
+          s_st[wid] = (uint32_t)r;
+          if (r == kCandInserted) {
+            PtF FP = load_ptf(c.ptf, p);
+            uint32_t f, g, s0 = w.slot[0];
+            cells_of(c, FP, &f, &g);
+            c.cell_hint[f] = s0;
+            c.cell_hint2[g] = s0;
+            c.point_hint[p] = s0;
+            c.st->anchor = s0;
+            atomicAdd(&s_stat[0], 1ull);
+            atomicAdd(&s_stat[3], (unsigned long long)nc);
+            atomicAdd(&s_stat[4], (unsigned long long)nb);
+          }
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid < (int)R) {
+        uint32_t st = s_st[tid], p = s_p[tid];
+        if (st != kCandEmpty) atomicAdd(&s_stat[2], 1ull);
+        if (st == kCandLost) atomicAdd(&s_stat[1], 1ull);
+        if (st == kCandLost || st == kCandWalkLimit) out[atomicAdd(&s_nout, 1u)] = p;
+        else if (st == kCandBig) big_out[atomicAdd(&c.st->q[kQBig], 1ull)] = p;
+        else if (st == kCandDup) atomicAdd(&c.st->n_dups, 1ull);
+      }
+      finish_round_block(c);
+    }
+    __syncthreads();
+    // the points of this pass that did not make it are the next pass
+    q = out;
+    m = s_nout;
+    out = (out == list_a) ? list_b : list_a;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    atomicAdd(&c.st->n_inserted, s_stat[0]);
+    atomicAdd(&c.st->n_conflicts, s_stat[1]);
+    atomicAdd(&c.st->n_attempts, s_stat[2]);
+    atomicAdd(&c.st->sum_cavity, s_stat[3]);
+    atomicAdd(&c.st->sum_ball, s_stat[4]);
+    atomicAdd(&c.st->sum_walk, s_stat[5]);
+    if (m > 0) raise_error(c.st, kErrInternal, 0xF000u);
+  }
+}
+
+// Wave of each vertex of one BRIO round: its hash rank inside the round (a uniformly random
+// order) against the cumulative wave ends; the stable sort by wave keeps the Moore order.
+__global__ void k_wave_keys(uint32_t vbegin, uint64_t m, uint64_t base, uint64_t rank0,
+                            const uint32_t* __restrict__ perm, const uint32_t* __restrict__ rank,
+                            const uint32_t* __restrict__ cum, int nwaves, uint64_t* keys, uint32_t* vals) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v = vbegin + (uint32_t)i;
+    uint64_t r = rank[perm[v - base]] - rank0;
+    int lo = 0, hi = nwaves - 1;
+    while (lo < hi) {
+      int mid = (lo + hi) / 2;
+      if (r < cum[mid]) hi = mid;
+      else lo = mid + 1;
+    }
+    keys[i] = (uint64_t)lo;
+    vals[i] = v;
   }
 }
 
@@ -467,14 +643,25 @@ __global__ void k_init(Ctx c, uint32_t vbegin, uint32_t vend, uint8_t* vflag) {
   c.st->n_inserted += 4;
 }
 
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);  // x - hi is exact in double
+}
+
 __global__ void k_build_pts(const double* __restrict__ xyz, const uint32_t* __restrict__ perm,
                             const uint8_t* __restrict__ dup, uint64_t n, uint64_t base,
-                            Pt* pts, uint8_t* vflag, uint32_t* point_hint) {
+                            Pt* pts, PtF* ptf, uint8_t* vflag, uint32_t* point_hint) {
   for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
        s += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = perm[s];
-    pts[base + s] = make_pt(xyz[3 * (uint64_t)i], xyz[3 * (uint64_t)i + 1], xyz[3 * (uint64_t)i + 2],
-                                 (double)(base + i));
+    double x = xyz[3 * (uint64_t)i], y = xyz[3 * (uint64_t)i + 1], z = xyz[3 * (uint64_t)i + 2];
+    pts[base + s] = make_pt(x, y, z, (double)(base + i));
+    PtF f;
+    split_df(x, f.hx, f.lx);
+    split_df(y, f.hy, f.ly);
+    split_df(z, f.hz, f.lz);
+    f.hw = f.lw = 0.0f;
+    ptf[base + s] = f;
     vflag[base + s] = dup[i];
     point_hint[base + s] = kNone;
   }
@@ -542,9 +729,29 @@ __global__ void k_eval_predicates(int kind, const double* pts, const int64_t* id
       q[k] = make_pt(pts[15 * i + 3 * k], pts[15 * i + 3 * k + 1], pts[15 * i + 3 * k + 2],
                           ids ? (double)ids[5 * i + k] : 0.0);
     int s;
-    if (kind == 0) s = orient3d(q[0], q[1], q[2], q[3], st);
-    else if (kind == 1) s = insphere(q[0], q[1], q[2], q[3], q[4], st);
-    else s = insphere_sos(q[0], q[1], q[2], q[3], q[4], st);
+    if (kind <= 2) {
+      if (kind == 0) s = orient3d(q[0], q[1], q[2], q[3], st);
+      else if (kind == 1) s = insphere(q[0], q[1], q[2], q[3], q[4], st);
+      else s = insphere_sos(q[0], q[1], q[2], q[3], q[4], st);
+    } else {
+      // the kernels' pipeline: FP32 stage on the double-float copy, then FP64 + exact
+      PtF f[5];
+      double cm = 0.0;
+      for (int k = 0; k < 5; ++k) {
+        split_df(q[k].x, f[k].hx, f[k].lx);
+        split_df(q[k].y, f[k].hy, f[k].ly);
+        split_df(q[k].z, f[k].hz, f[k].lz);
+        cm = fmax(cm, fmax(fabs(q[k].x), fmax(fabs(q[k].y), fabs(q[k].z))));
+      }
+      float eta = (float)(ldexp(cm, -44) * 1.0001 + 1e-38);
+      if (kind == 3) {
+        s = orient3d_f(f[0], f[1], f[2], f[3], eta);
+        if (s == 0) s = orient3d(q[0], q[1], q[2], q[3], st);
+      } else {
+        s = insphere_f(f[0], f[1], f[2], f[3], f[4], eta);
+        if (s == 0) s = insphere_sos(q[0], q[1], q[2], q[3], q[4], st);
+      }
+    }
     out[i] = (int8_t)s;
   }
 }
@@ -575,6 +782,8 @@ struct dt_handle {
   cudaStream_t stream = nullptr;
   OrderWS ows;
   Pt* pts = nullptr;
+  PtF* ptf = nullptr;
+  double cmax = 0.0;  // largest |coordinate| so far (sets the FP32 stage's eta)
   uint8_t* vflag = nullptr;
   uint32_t* point_hint = nullptr;
   uint64_t n_pts = 0, cap_pts = 0;
@@ -602,7 +811,12 @@ struct dt_handle {
   double* bbox_dev = nullptr;
   bool has_mesh = false;
   uint64_t last_n = 0;
-  double alpha = 0.03;
+  double alpha = 0.03;   // candidates per round = alpha * mesh vertices
+  double gamma = 0.3;    // wave size = gamma * mesh vertices
+  double alpha_cta = 0.1;  // candidates per round of the one-block engine (at most 16)
+  uint32_t* wlist = nullptr;
+  uint32_t* wave_cum = nullptr;
+  uint64_t cap_w = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> prof_events;
   unsigned long long next_stamp = 1;
@@ -632,6 +846,9 @@ Ctx make_ctx(dt_handle* h) {
   c.tets = h->tets;
   c.claim = h->claim;
   c.pts = h->pts;
+  c.ptf = h->ptf;
+  // eta = 2^-44 max|x| plus the spacing of FP32 subnormals (see predicates.cuh)
+  c.eta = (float)(std::ldexp(h->cmax, -44) * 1.0001 + 1e-38);
   c.freelist = h->freelist;
   c.pending = h->pending;
   c.cell_hint = h->cell_hint;
@@ -666,6 +883,7 @@ int reserve_points(dt_handle* h, uint64_t total) {
   if (total <= h->cap_pts) return DT_OK;
   uint64_t nc = std::max<uint64_t>(total, h->cap_pts + h->cap_pts / 2);
   if (grow(h->pts, h->n_pts, nc, h->stream) != cudaSuccess) return DT_ENOMEM;
+  if (grow(h->ptf, h->n_pts, nc, h->stream) != cudaSuccess) return DT_ENOMEM;
   if (grow(h->vflag, h->n_pts, nc, h->stream) != cudaSuccess) return DT_ENOMEM;
   if (grow(h->point_hint, h->n_pts, nc, h->stream) != cudaSuccess) return DT_ENOMEM;
   h->cap_pts = nc;
@@ -677,11 +895,11 @@ int reserve_tets(dt_handle* h, uint64_t total_pts) {
   uint64_t need = (uint64_t)(f * (double)total_pts) + 4096;
   if (need > 0x3FFFFFFFull) need = 0x3FFFFFFFull;  // 4t + facet fits 32 bits
   if (need <= h->cap_tets) return DT_OK;
-  uint64_t old = h->cap_tets;
   unsigned long long bump = h->has_mesh ? h->st_host->bump : 0;
   if (grow(h->tets, bump, need, h->stream) != cudaSuccess) return DT_ENOMEM;
   if (grow(h->claim, bump, need, h->stream) != cudaSuccess) return DT_ENOMEM;
-  cudaMemsetAsync(h->claim + old, 0, (need - old) * sizeof(unsigned long long), h->stream);
+  // claim words of slots not yet handed out start at zero (below every priority)
+  cudaMemsetAsync(h->claim + bump, 0, (need - bump) * sizeof(unsigned long long), h->stream);
   uint64_t nf = need / 4 + 4096;
   uint64_t fold = h->has_mesh ? h->st_host->free_avail : 0;
   if (grow(h->freelist, fold, nf, h->stream) != cudaSuccess) return DT_ENOMEM;
@@ -710,6 +928,13 @@ int reserve_rounds(dt_handle* h, uint64_t qcap) {
     size_t huge = carve(nullptr, kHugeHash, kHugeC, kHugeF, kHugeEdge, nullptr);
     if (cudaMalloc(&h->hugemem, huge)) return DT_ENOMEM;
     carve(h->hugemem, kHugeHash, kHugeC, kHugeF, kHugeEdge, &h->hugews);
+  }
+  if (!h->wave_cum && cudaMalloc(&h->wave_cum, 256 * 4) != cudaSuccess) return DT_ENOMEM;
+  if (qcap > h->cap_w) {
+    cudaFree(h->wlist);
+    h->wlist = nullptr;
+    if (cudaMalloc(&h->wlist, qcap * 4) != cudaSuccess) return DT_ENOMEM;
+    h->cap_w = qcap;
   }
   if (qcap > h->cap_q) {
     for (auto& qb : h->queue) {
@@ -804,63 +1029,113 @@ int run_big(dt_handle* h, const Ctx& c) {
   return DT_OK;
 }
 
-// Inserts the vertices [vbegin, vend) (one BRIO round, Moore order) by passes of concurrent
-// rounds; failed points are re-keyed with a re-partition transform and retried (Section 3.3).
-int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend) {
-  Ctx c = make_ctx(h);
-  const uint32_t* q = nullptr;
-  uint32_t qbase = vbegin;
-  uint64_t m = vend - vbegin;
-  uint32_t pass = 0;
-  uint32_t max_rounds = h->cfg.max_rounds ? h->cfg.max_rounds : (1u << 22);
-  int stalled = 0;
-  while (m > 0) {
-    uint64_t mesh = h->st_host->n_inserted;
-    uint64_t before = h->st_host->n_inserted + h->st_host->n_dups;
-    uint32_t R = choose_segments(h, mesh, m);
-    uint64_t L = (m + R - 1) / R;
-    int rc = set_queue_lengths(h, {kQNext, kQBig, kQHuge});
-    if (rc != DT_OK) return rc;
-    const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0;
-    if (prof) {
-      while (h->prof_events.size() < 6 * L) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return DT_ECUDA;
-        h->prof_events.push_back(e);
-      }
+// One pass: rounds over q[0..m) (or the vertex range qbase + [0, m)) split into R segments of
+// length L (segment s offers q[s*L + j] in round j), then the large cavities of the pass.
+int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next) {
+  uint64_t mesh = h->st_host->n_inserted;
+  uint32_t R = choose_segments(h, mesh, m);
+  uint64_t L = (m + R - 1) / R;
+  int rc = reset_next ? set_queue_lengths(h, {kQNext, kQBig, kQHuge}) : set_queue_lengths(h, {kQBig, kQHuge});
+  if (rc != DT_OK) return rc;
+  const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0;
+  if (prof) {
+    while (h->prof_events.size() < 6 * L) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return DT_ECUDA;
+      h->prof_events.push_back(e);
     }
+  }
+  for (uint64_t j = 0; j < L; ++j) {
+    RoundIO io{q, qbase, m, L, j, R, h->queue[kQNext], kQNext, h->queue[kQBig], kQBig};
+    launch_round(h, c, io, false, j);
+  }
+  h->stats.n_passes++;
+  if ((rc = sync_state(h)) != DT_OK) return rc;
+  if (cudaGetLastError() != cudaSuccess) return DT_ECUDA;
+  if (prof) {
     for (uint64_t j = 0; j < L; ++j) {
-      RoundIO io{q, qbase, m, L, j, R, h->queue[kQNext], kQNext, h->queue[kQBig], kQBig};
-      launch_round(h, c, io, false, j);
+      float a = 0, b = 0, cc = 0;
+      cudaEventElapsedTime(&a, h->prof_events[6 * j], h->prof_events[6 * j + 1]);
+      cudaEventElapsedTime(&b, h->prof_events[6 * j + 2], h->prof_events[6 * j + 3]);
+      cudaEventElapsedTime(&cc, h->prof_events[6 * j + 4], h->prof_events[6 * j + 5]);
+      h->stats.ms_walk += a;
+      h->stats.ms_cavity += b;
+      h->stats.ms_insert_k += cc;
+      h->stats.n_profiled++;
     }
-    h->stats.n_passes++;
-    if ((rc = sync_state(h)) != DT_OK) return rc;
-    if (cudaGetLastError() != cudaSuccess) return DT_ECUDA;
-    if (prof) {
-      for (uint64_t j = 0; j < L; ++j) {
-        float a = 0, b = 0, cc = 0;
-        cudaEventElapsedTime(&a, h->prof_events[6 * j], h->prof_events[6 * j + 1]);
-        cudaEventElapsedTime(&b, h->prof_events[6 * j + 2], h->prof_events[6 * j + 3]);
-        cudaEventElapsedTime(&cc, h->prof_events[6 * j + 4], h->prof_events[6 * j + 5]);
-        h->stats.ms_walk += a;
-        h->stats.ms_cavity += b;
-        h->stats.ms_insert_k += cc;
-        h->stats.n_profiled++;
-      }
-    }
-    uint64_t nq = h->st_host->q[kQNext];
-    if ((rc = run_big(h, c)) != DT_OK) return rc;
+  }
+  return run_big(h, c);
+}
+
+// The first BRIO round of a new triangulation on one thread block (see k_cta_insert).
+int run_cta_round(dt_handle* h, uint32_t vbegin, uint32_t vend) {
+  Ctx c = make_ctx(h);
+  Ctx cc = c;
+  cc.coherent = 1;
+  int rc = set_queue_lengths(h, {kQBig, kQHuge});
+  if (rc != DT_OK) return rc;
+  size_t smem = sizeof(CtaWarpSmem) * kCtaWarps;
+  if (cudaFuncSetAttribute(k_cta_insert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return DT_ECUDA;
+  k_cta_insert<<<1, kCtaWarps * 32, smem, h->stream>>>(cc, vbegin, vend - vbegin, h->vflag, h->queue[kQNext],
+                                                        h->queue[kQBig2], h->queue[kQBig], (float)h->alpha_cta,
+                                                        1u << 16);
+  ++g_kernel_launches;
+  h->stats.n_passes++;
+  if ((rc = sync_state(h)) != DT_OK) return rc;
+  return run_big(h, c);
+}
+
+// Inserts the vertices [vbegin, vend) (BRIO round `round`, Moore order). The round is split
+// into waves of about gamma * (mesh size) points, each a uniformly random subset kept in
+// Moore order, so the number of concurrent insertions can follow the mesh as it grows. Points
+// that lose a conflict are retried after the last wave, re-keyed with a re-partition
+// transform (Section 3.3) until none is left.
+int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint64_t base) {
+  Ctx c = make_ctx(h);
+  cudaStream_t s = h->stream;
+  uint64_t m = vend - vbegin;
+  uint32_t max_rounds = h->cfg.max_rounds ? h->cfg.max_rounds : (1u << 22);
+  // wave boundaries (cumulative ranks inside the round)
+  std::vector<uint32_t> cum;
+  double N = (double)std::max<uint64_t>(h->st_host->n_inserted, 4);
+  uint64_t acc = 0;
+  while (acc < m && cum.size() < 255) {
+    uint64_t w = (uint64_t)std::max(1.0, std::ceil(h->gamma * N));
+    acc = std::min<uint64_t>(m, acc + w);
+    cum.push_back((uint32_t)acc);
+    N += (double)w;
+  }
+  cum.back() = (uint32_t)m;
+  if (cudaMemcpyAsync(h->wave_cum, cum.data(), cum.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return DT_ECUDA;
+  uint64_t rank0 = round == 0 ? 0 : brio_round_end(round - 1);
+  k_wave_keys<<<grid_for(m, 256), 256, 0, s>>>(vbegin, m, base, rank0, h->ows.perm, h->ows.rank, h->wave_cum,
+                                                (int)cum.size(), h->ows.k0, h->ows.v0);
+  ++g_kernel_launches;
+  bool alt = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, m, 8, h->ows.hist, s);
+  cudaMemcpyAsync(h->wlist, alt ? h->ows.v1 : h->ows.v0, m * 4, cudaMemcpyDeviceToDevice, s);
+  int rc = set_queue_lengths(h, {kQNext});
+  if (rc != DT_OK) return rc;
+  uint64_t off = 0;
+  for (uint32_t e : cum) {
+    if ((rc = run_pass(h, c, h->wlist + off, 0, e - off, false)) != DT_OK) return rc;
+    off = e;
+  }
+  uint64_t nq = h->st_host->q[kQNext];
+  uint32_t pass = 0;
+  int stalled = 0;
+  while (nq > 0) {
     if (h->stats.n_rounds > max_rounds) return DT_ELIMIT;
-    if (nq == 0) break;
+    uint64_t before = h->st_host->n_inserted + h->st_host->n_dups;
+    transformed_keys(h->pts, h->queue[kQNext], nq, h->bbox_dev, h->cfg.seed + 0x51ED2701ull * (pass + 1) + vbegin,
+                     h->ows.k0, h->ows.v0, s);
+    bool a2 = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, nq, 64, h->ows.hist, s);
+    if ((rc = run_pass(h, c, a2 ? h->ows.v1 : h->ows.v0, 0, nq, true)) != DT_OK) return rc;
+    nq = h->st_host->q[kQNext];
     // a pass that inserted nothing three times in a row is a bug, not a schedule
     stalled = (h->st_host->n_inserted + h->st_host->n_dups == before) ? stalled + 1 : 0;
     if (stalled >= 3) return DT_ELIMIT;
-    // re-partition the failed points: transformed keys, then sort (Section 3.3)
-    transformed_keys(h->pts, h->queue[kQNext], nq, h->bbox_dev,
-                     h->cfg.seed + 0x51ED2701ull * (pass + 1) + vbegin, h->ows.k0, h->ows.v0, h->stream);
-    bool alt = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, nq, 64, h->ows.hist, h->stream);
-    q = alt ? h->ows.v1 : h->ows.v0;
-    m = nq;
     ++pass;
   }
   return DT_OK;
@@ -878,13 +1153,14 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
   if ((rc = reserve_points(h, base + n)) != DT_OK) return rc;
   if ((rc = reserve_tets(h, base + n)) != DT_OK) return rc;
   if ((rc = reserve_rounds(h, n + 1024)) != DT_OK) return rc;
-  k_build_pts<<<grid_for(n, 256), 256, 0, s>>>(xyz, h->ows.perm, h->ows.dup, n, base, h->pts, h->vflag,
-                                                h->point_hint);
+  k_build_pts<<<grid_for(n, 256), 256, 0, s>>>(xyz, h->ows.perm, h->ows.dup, n, base, h->pts, h->ptf,
+                                                h->vflag, h->point_hint);
   ++g_kernel_launches;
+  double bb[6];
+  if (cudaMemcpyAsync(bb, h->ows.bbox, 48, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DT_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
+  for (int k = 0; k < 6; ++k) h->cmax = std::max(h->cmax, std::fabs(bb[k]));
   if (!h->has_mesh) {
-    double bb[6];
-    if (cudaMemcpyAsync(bb, h->ows.bbox, 48, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DT_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
     if (!h->bbox_dev && cudaMalloc(&h->bbox_dev, 48) != cudaSuccess) return DT_ENOMEM;
     cudaMemcpyAsync(h->bbox_dev, h->ows.bbox, 48, cudaMemcpyDeviceToDevice, s);
     // hint grid: about 8 points per cell, at most 2^24 cells
@@ -924,7 +1200,11 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
     uint64_t b = r == 0 ? 0 : brio_round_end(r - 1);
     if (b >= n) break;
     uint64_t e = std::min<uint64_t>(brio_round_end(r), n);
-    if ((rc = run_brio_round(h, (uint32_t)(base + b), (uint32_t)(base + e))) != DT_OK) return rc;
+    if (r == 0 && h->st_host->n_inserted <= 4 && !std::getenv("DT_NO_CTA"))
+      rc = run_cta_round(h, (uint32_t)(base + b), (uint32_t)(base + e));
+    else
+      rc = run_brio_round(h, (uint32_t)(base + b), (uint32_t)(base + e), r, base);
+    if (rc != DT_OK) return rc;
   }
   cudaEventRecord(h->ev[2], s);
   if ((rc = sync_state(h)) != DT_OK) return rc;
@@ -979,6 +1259,8 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (cfg) h->cfg = *cfg;
   h->stream = (cudaStream_t)h->cfg.stream;
   if (const char* a = std::getenv("DT_ALPHA")) h->alpha = std::atof(a);
+  if (const char* g = std::getenv("DT_GAMMA")) h->gamma = std::atof(g);
+  if (const char* a = std::getenv("DT_ALPHA_CTA")) h->alpha_cta = std::atof(a);
   bool ok = cudaMalloc(&h->st, sizeof(DevState)) == cudaSuccess &&
             cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess;
   for (auto& e : h->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
@@ -1003,6 +1285,7 @@ int dt_clear(dt_handle* h) {
   h->has_mesh = false;
   h->n_pts = 0;
   h->last_n = 0;
+  h->cmax = 0.0;
   h->last_dev_error = h->last_dev_info = 0;
   h->stats = dt_stats{};
   h->launches0 = g_kernel_launches;
@@ -1151,6 +1434,7 @@ void dt_destroy(dt_handle* h) {
   else cudaDeviceSynchronize();
   order_ws_free(h->ows);
   cudaFree(h->pts);
+  cudaFree(h->ptf);
   cudaFree(h->vflag);
   cudaFree(h->point_hint);
   cudaFree(h->tets);
@@ -1168,6 +1452,8 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->cand_nb);
   cudaFree(h->scratch);
   for (auto& qb : h->queue) cudaFree(qb);
+  cudaFree(h->wlist);
+  cudaFree(h->wave_cum);
   cudaFree(h->bigmem);
   cudaFree(h->hugemem);
   cudaFree(h->bbox_dev);
@@ -1193,14 +1479,15 @@ const char* dt_strerror(int code) {
 
 int dt_eval_predicates(int kind, const double* pts_dev, const int64_t* ids_dev, int8_t* out_dev, uint64_t n,
                        void* stream) {
-  if (kind < 0 || kind > 2 || (n > 0 && (!pts_dev || !out_dev)) || (kind == 2 && n > 0 && !ids_dev))
+  if (kind < 0 || kind > 4 || (n > 0 && (!pts_dev || !out_dev)) || ((kind == 2 || kind == 4) && n > 0 && !ids_dev))
     return DT_EINVAL;
   if (n == 0) return DT_OK;
   cudaStream_t s = (cudaStream_t)stream;
   DevState* st = nullptr;
   if (cudaMalloc(&st, sizeof(DevState)) != cudaSuccess) return DT_ENOMEM;
   cudaMemsetAsync(st, 0, sizeof(DevState), s);
-  k_eval_predicates<<<grid_for(n, 128), 128, 0, s>>>(kind, pts_dev, kind == 2 ? ids_dev : nullptr, out_dev, n, st);
+  k_eval_predicates<<<grid_for(n, 128), 128, 0, s>>>(kind, pts_dev, (kind == 2 || kind == 4) ? ids_dev : nullptr,
+                                                     out_dev, n, st);
   ++g_kernel_launches;
   DevState hs;
   cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s);

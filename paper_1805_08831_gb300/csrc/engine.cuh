@@ -40,7 +40,9 @@ constexpr int kHash = 256;  // visited-set slots per warp (shared-memory path)
 struct Ctx {
   Tet* tets;
   unsigned long long* claim;
-  const Pt* pts;  // .w = input index (the perturbation order)
+  const Pt* pts;   // exact coordinates; .w = input index (the perturbation order)
+  const PtF* ptf;  // double-float copy for the FP32 first stage of the predicates
+  float eta;       // absolute error of a double-float difference (see predicates.cuh)
   uint32_t* freelist;
   uint32_t* pending;
   uint32_t* cell_hint;    // fine grid: a recent tetrahedron per cell
@@ -112,8 +114,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Fine and coarse hint-grid cells of P.
-__device__ __forceinline__ void cells_of(const Ctx& c, Pt P, uint32_t* fine, uint32_t* coarse) {
-  double x[3] = {P.x, P.y, P.z};
+__device__ __forceinline__ void cells_of(const Ctx& c, const PtF& P, uint32_t* fine, uint32_t* coarse) {
+  double x[3] = {(double)P.hx, (double)P.hy, (double)P.hz};
   double lim = (double)((1u << c.cb) - 1u);
   uint32_t q[3];
   for (int k = 0; k < 3; ++k) {
@@ -138,9 +140,26 @@ __device__ __forceinline__ void after_pos(int i, int& a, int& b, int& c) {
 __device__ __forceinline__ Pt sel4(int i, int k, Pt P, Pt V) { return i == k ? P : V; }
 
 // ------------------------------------------------------------------ walk (Section 2.1)
-// Returns kCandLocated (*t_out in conflict with P), kCandWalkLimit (*t_out = where it stopped)
-// or kCandDup (P equals a vertex of the tetrahedron reached).
-__device__ int walk_point(const Ctx& c, Pt P, uint32_t start, uint32_t salt, uint32_t anchor,
+__device__ __forceinline__ const PtF& self4(int i, int k, const PtF& P, const PtF& V) { return i == k ? P : V; }
+__device__ __forceinline__ Pt self4d(int i, int k, const Pt& P, const Pt& V) { return i == k ? P : V; }
+
+__device__ __forceinline__ bool same_f(const PtF& a, const PtF& b) {
+  return a.hx == b.hx && a.hy == b.hy && a.hz == b.hz && a.lx == b.lx && a.ly == b.ly && a.lz == b.lz;
+}
+
+// orient3d of tetrahedron vertices v[] with vertex i replaced by the query p (FP32 stage first).
+__device__ __forceinline__ int orient_replace(const Ctx& c, const uint4& v, int i, uint32_t p, const PtF& FP,
+                                              const PtF& F0, const PtF& F1, const PtF& F2, const PtF& F3) {
+  int o = orient3d_f(self4(i, 0, FP, F0), self4(i, 1, FP, F1), self4(i, 2, FP, F2), self4(i, 3, FP, F3), c.eta);
+  if (o != 0) return o;
+  Pt P = load_pt(c.pts, p);
+  Pt V0 = load_pt(c.pts, v.x), V1 = load_pt(c.pts, v.y), V2 = load_pt(c.pts, v.z), V3 = load_pt(c.pts, v.w);
+  return orient3d(self4d(i, 0, P, V0), self4d(i, 1, P, V1), self4d(i, 2, P, V2), self4d(i, 3, P, V3), c.st);
+}
+
+// Returns kCandLocated (*t_out in conflict with p), kCandWalkLimit (*t_out = where it stopped)
+// or kCandDup (p equals a vertex of the tetrahedron reached).
+__device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32_t start, uint32_t salt, uint32_t anchor,
                           uint32_t max_steps, uint32_t* t_out, uint32_t* steps_out) {
   uint32_t t = start;
   Tet T;
@@ -177,28 +196,30 @@ __device__ int walk_point(const Ctx& c, Pt P, uint32_t start, uint32_t salt, uin
   }
   uint32_t prev = kNone;
   uint32_t steps = 0;
-  Pt V0, V1, V2, V3;
   for (;;) {
-    if (ghost_pos(T.v) >= 0) break;  // entered a ghost through a facet that sees P
-    V0 = load_pt(c.pts, T.v.x);
-    V1 = load_pt(c.pts, T.v.y);
-    V2 = load_pt(c.pts, T.v.z);
-    V3 = load_pt(c.pts, T.v.w);
+    if (ghost_pos(T.v) >= 0) break;  // entered a ghost through a facet that sees p
+    PtF F0 = load_ptf(c.ptf, T.v.x), F1 = load_ptf(c.ptf, T.v.y), F2 = load_ptf(c.ptf, T.v.z),
+        F3 = load_ptf(c.ptf, T.v.w);
     int exit = -1;
     int s0 = (salt + steps) & 3;
     for (int k = 0; k < 4; ++k) {
       int i = (s0 + k) & 3;
       uint32_t nb = get4(T.n, i) >> 2;
-      if (nb == prev) continue;  // P is on this tetrahedron's side of the facet just crossed
-      int o = orient3d(sel4(i, 0, P, V0), sel4(i, 1, P, V1), sel4(i, 2, P, V2), sel4(i, 3, P, V3), c.st);
-      if (o < 0) {
+      if (nb == prev) continue;  // p is on this tetrahedron's side of the facet just crossed
+      if (orient_replace(c, T.v, i, p, FP, F0, F1, F2, F3) < 0) {
         exit = i;
         break;
       }
     }
     if (exit < 0) {
-      bool dup = (V0.x == P.x && V0.y == P.y && V0.z == P.z) || (V1.x == P.x && V1.y == P.y && V1.z == P.z) ||
-                 (V2.x == P.x && V2.y == P.y && V2.z == P.z) || (V3.x == P.x && V3.y == P.y && V3.z == P.z);
+      bool dup = false;
+      if (same_f(F0, FP) || same_f(F1, FP) || same_f(F2, FP) || same_f(F3, FP)) {
+        Pt P = load_pt(c.pts, p);
+        for (int k = 0; k < 4; ++k) {
+          Pt V = load_pt(c.pts, get4(T.v, k));
+          dup = dup || (V.x == P.x && V.y == P.y && V.z == P.z);
+        }
+      }
       *t_out = t;
       *steps_out = steps;
       return dup ? kCandDup : kCandLocated;
@@ -225,34 +246,42 @@ __device__ int walk_point(const Ctx& c, Pt P, uint32_t start, uint32_t salt, uin
 }
 
 // ------------------------------------------------------------------ conflict test
-// Membership of tetrahedron u in the cavity of P: perturbed insphere for a finite tetrahedron;
-// for a ghost, P strictly beyond its hull facet, or on the facet's plane and inside the
+// Perturbed insphere of a finite tetrahedron and p: negative = p inside (FP32 stage first).
+__device__ __forceinline__ bool inside_finite(const Ctx& c, const uint4& v, uint32_t p, const PtF& FP) {
+  PtF A = load_ptf(c.ptf, v.x), B = load_ptf(c.ptf, v.y), C = load_ptf(c.ptf, v.z), D = load_ptf(c.ptf, v.w);
+  int s = insphere_f(A, B, C, D, FP, c.eta);
+  if (s != 0) return s < 0;
+  Pt a = load_pt(c.pts, v.x), b = load_pt(c.pts, v.y), d = load_pt(c.pts, v.z), e = load_pt(c.pts, v.w);
+  return insphere_sos(a, b, d, e, load_pt(c.pts, p), c.st) < 0;
+}
+
+// Membership of tetrahedron u in the cavity of p: perturbed insphere for a finite tetrahedron;
+// for a ghost, p strictly beyond its hull facet, or on the facet's plane and inside the
 // perturbed sphere of the finite neighbour across it (Section 2.6).
-__device__ bool in_conflict(const Ctx& c, uint32_t u, Pt P) {
+__device__ bool in_conflict(const Ctx& c, uint32_t u, uint32_t p, const PtF& FP) {
   Tet U = tet_at(c, u);
   if (!tet_sane(c, U) || tet_dead(U.v)) {
     raise_error(c.st, kErrInternal, 0xB000u);
     return false;
   }
   int g = ghost_pos(U.v);
-  if (g < 0) {
-    Pt a = load_pt(c.pts, U.v.x), b = load_pt(c.pts, U.v.y), d = load_pt(c.pts, U.v.z),
-            e = load_pt(c.pts, U.v.w);
-    return insphere_sos(a, b, d, e, P, c.st) < 0;
+  if (g < 0) return inside_finite(c, U.v, p, FP);
+  PtF q[4];
+  for (int k = 0; k < 4; ++k) q[k] = (k == g) ? FP : load_ptf(c.ptf, get4(U.v, k));
+  int o = orient3d_f(q[0], q[1], q[2], q[3], c.eta);
+  if (o == 0) {
+    Pt r[4];
+    for (int k = 0; k < 4; ++k) r[k] = load_pt(c.pts, k == g ? p : get4(U.v, k));
+    o = orient3d(r[0], r[1], r[2], r[3], c.st);
   }
-  Pt q[4];
-  for (int k = 0; k < 4; ++k) q[k] = (k == g) ? P : load_pt(c.pts, get4(U.v, k));
-  int o = orient3d(q[0], q[1], q[2], q[3], c.st);
   if (o != 0) return o > 0;
-  uint32_t r = get4(U.n, g) >> 2;
-  Tet R = tet_at(c, r);
+  uint32_t rr = get4(U.n, g) >> 2;
+  Tet R = tet_at(c, rr);
   if (!tet_sane(c, R) || ghost_pos(R.v) >= 0) {
     raise_error(c.st, kErrInternal, 0xB001u);
     return false;
   }
-  Pt a = load_pt(c.pts, R.v.x), b = load_pt(c.pts, R.v.y), d = load_pt(c.pts, R.v.z),
-          e = load_pt(c.pts, R.v.w);
-  return insphere_sos(a, b, d, e, P, c.st) < 0;
+  return inside_finite(c, R.v, p, FP);
 }
 
 // ------------------------------------------------------------------ visited set
@@ -285,14 +314,14 @@ __device__ __forceinline__ bool ws_insert(const CavWS& w, uint32_t key, uint8_t 
 // ------------------------------------------------------------------ cavity (warp)
 // Returns kCandLocated (C in w.clist[0..nc), boundary facets in w.blist[0..nb)), kCandLost
 // (saw a higher-priority claim) or kCandBig (exceeds this workspace).
-__device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, Pt P,
+__device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uint32_t p, const PtF& FP,
                            unsigned long long prio, int* nc_out, int* nb_out) {
   const int lane = threadIdx.x & 31;
   for (uint32_t i = lane; i <= w.hmask; i += 32) w.hkey[i] = kNone;
   __syncwarp();
   int flag = 0;  // 1 lost, 2 big, 4 internal
   if (lane == 0) {
-    if (!in_conflict(c, t0, P)) flag |= 4;
+    if (!in_conflict(c, t0, p, FP)) flag |= 4;
     w.clist[0] = t0;
     ws_insert(w, t0, 1);
     if (atomicMax(&c.claim[t0], prio) > prio) flag |= 1;
@@ -325,7 +354,7 @@ __device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, Pt P,
     bool is_leader = need && lane == leader;
     int res = 0, myflag = 0;
     if (is_leader) {
-      res = in_conflict(c, u, P) ? 1 : 2;
+      res = in_conflict(c, u, p, FP) ? 1 : 2;
       if (atomicMax(&c.claim[u], prio) > prio) myflag |= 1;
       if (!ws_insert(w, u, (uint8_t)res)) myflag |= 2;
     }

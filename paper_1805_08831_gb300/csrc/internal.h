@@ -24,6 +24,7 @@ struct OrderWS {
   uint8_t* rounds = nullptr;     // BRIO round per input index
   uint8_t* dup = nullptr;        // 1 = exact duplicate of a smaller input index
   uint32_t* perm = nullptr;      // insertion order: s-th point -> input index
+  uint32_t* rank = nullptr;      // BRIO hash rank per input index
   uint32_t* hist = nullptr;      // radix histograms / scan scratch
   uint64_t hist_cap = 0;
   double* bbox = nullptr;        // [6] lo xyz, hi xyz

@@ -216,7 +216,7 @@ __global__ void k_brio_hash(uint64_t n, uint64_t seed, uint64_t* keys, uint32_t*
   }
 }
 
-__global__ void k_brio_assign(const uint32_t* sorted_idx, uint64_t n, uint8_t* rounds) {
+__global__ void k_brio_assign(const uint32_t* sorted_idx, uint64_t n, uint8_t* rounds, uint32_t* rank) {
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
        r += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t end = 2048;
@@ -226,6 +226,7 @@ __global__ void k_brio_assign(const uint32_t* sorted_idx, uint64_t n, uint8_t* r
       ++k;
     }
     rounds[sorted_idx[r]] = k;
+    rank[sorted_idx[r]] = (uint32_t)r;
   }
 }
 
@@ -437,6 +438,7 @@ cudaError_t order_ws_reserve(OrderWS& ws, uint64_t n) {
   if ((e = cudaMalloc(&ws.rounds, c)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&ws.dup, c)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&ws.perm, c * 4)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&ws.rank, c * 4)) != cudaSuccess) return e;
   ws.hist_cap = radix_hist_entries(c);
   if ((e = cudaMalloc(&ws.hist, ws.hist_cap * 4)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&ws.bbox, 6 * 8)) != cudaSuccess) return e;
@@ -455,6 +457,7 @@ void order_ws_free(OrderWS& ws) {
   cudaFree(ws.rounds);
   cudaFree(ws.dup);
   cudaFree(ws.perm);
+  cudaFree(ws.rank);
   cudaFree(ws.hist);
   cudaFree(ws.bbox);
   cudaFree(ws.partial);
@@ -485,7 +488,7 @@ int order_points_ws(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, c
   k_brio_hash<<<g, 256, 0, s>>>(n, seed, ws.k0, ws.v0);
   ++g_kernel_launches;
   bool alt2 = radix_sort_pairs(ws.k0, ws.v0, ws.k1, ws.v1, n, 64, ws.hist, s);
-  k_brio_assign<<<g, 256, 0, s>>>(alt2 ? ws.v1 : ws.v0, n, ws.rounds);
+  k_brio_assign<<<g, 256, 0, s>>>(alt2 ? ws.v1 : ws.v0, n, ws.rounds, ws.rank);
   ++g_kernel_launches;
   // stable sort of the key order by round
   k_round_keys<<<g, 256, 0, s>>>(ws.perm, n, ws.rounds, ws.k0);
@@ -533,7 +536,8 @@ constexpr size_t kOffHist = kOffDup + align256(kNoAllocMax);
 constexpr size_t kOffBox = kOffHist + align256(kNoAllocHist * 4);
 constexpr size_t kOffPart = kOffBox + align256(6 * 8);
 constexpr size_t kOffBad = kOffPart + align256(kBoxBlocks * 6 * 8);
-constexpr size_t kNoAllocBytes = kOffBad + 256;
+constexpr size_t kOffRank = kOffBad + 256;
+constexpr size_t kNoAllocBytes = kOffRank + align256(kNoAllocMax * 4);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -581,5 +585,6 @@ extern "C" int dt_order_noalloc(const double* xyz_dev, uint64_t n, uint64_t seed
   ws.bbox = reinterpret_cast<double*>(base + kOffBox);
   ws.partial = reinterpret_cast<double*>(base + kOffPart);
   ws.bad = reinterpret_cast<unsigned int*>(base + kOffBad);
+  ws.rank = reinterpret_cast<uint32_t*>(base + kOffRank);
   return order_points_ws(xyz_dev, n, seed, ws, static_cast<cudaStream_t>(stream));
 }

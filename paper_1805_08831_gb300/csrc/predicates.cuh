@@ -285,6 +285,97 @@ __device__ __noinline__ bool collinear_exact(Pt a, Pt b, Pt c, DevState* st) {
   return zero;
 }
 
+// ----------------------------------------------------------------- FP32 first stage
+// GB300 runs FP64 at about 1/64 of the FP32 rate, and converting FP64 to FP32 costs as much as
+// an FP64 operation. So every vertex also carries a double-float copy x = hi + lo (+ r,
+// |r| <= 2^-48 |x|), and the predicates first run in FP32 on it:
+//   differences D = fl(fl(hi_q - hi_a) + fl(lo_q - lo_a)) satisfy
+//   |D - (q - a)| <= 2.01 u |D| + eta,  u = 2^-24, eta = 2^-44 max|x| (+ subnormal slack);
+//   the determinant and its permanent P (sum of |monomials|) are evaluated in FP32; with
+//   k input factors and r roundings per monomial, |det_f - det| <= (2.01 k + r) u P +
+//   (k * #monomials) eta mmax^(k-1) to first order. orient3d: k = 3, r = 8, 6 monomials;
+//   insphere: k = 5, r = 16, 72 monomials. The constants below round these up (15 u, 28 u;
+//   20 eta, 400 eta). When the sign is not certain (or magnitudes leave FP32's normal range)
+//   the FP64 stage below decides.
+struct __align__(16) PtF {
+  float hx, hy, hz, hw;
+  float lx, ly, lz, lw;
+};
+
+constexpr float kU = 5.9604645e-08f;  // 2^-24
+constexpr float kOrientCf = 15.0f * kU;
+constexpr float kInsphereCf = 28.0f * kU;
+
+__device__ __forceinline__ PtF load_ptf(const PtF* P, uint32_t v) {
+  const float4* q = reinterpret_cast<const float4*>(P + v);
+  float4 a = __ldg(q), b = __ldg(q + 1);
+  PtF r;
+  r.hx = a.x; r.hy = a.y; r.hz = a.z; r.hw = a.w;
+  r.lx = b.x; r.ly = b.y; r.lz = b.z; r.lw = b.w;
+  return r;
+}
+
+__device__ __forceinline__ void diff_f(const PtF& q, const PtF& a, float& x, float& y, float& z) {
+  x = (q.hx - a.hx) + (q.lx - a.lx);
+  y = (q.hy - a.hy) + (q.ly - a.ly);
+  z = (q.hz - a.hz) + (q.lz - a.lz);
+}
+
+// 1 / -1 when certain, 0 when the FP64 stage must decide.
+__device__ __forceinline__ int orient3d_f(const PtF& a, const PtF& b, const PtF& c, const PtF& d, float eta) {
+  float ux, uy, uz, vx, vy, vz, wx, wy, wz;
+  diff_f(b, a, ux, uy, uz);
+  diff_f(c, a, vx, vy, vz);
+  diff_f(d, a, wx, wy, wz);
+  float m0 = vy * wz - vz * wy, m1 = vx * wz - vz * wx, m2 = vx * wy - vy * wx;
+  float det = ux * m0 - uy * m1 + uz * m2;
+  float perm = fabsf(ux) * (fabsf(vy * wz) + fabsf(vz * wy)) + fabsf(uy) * (fabsf(vx * wz) + fabsf(vz * wx)) +
+               fabsf(uz) * (fabsf(vx * wy) + fabsf(vy * wx));
+  float mm = fmaxf(fmaxf(fmaxf(fabsf(ux), fabsf(uy)), fmaxf(fabsf(uz), fabsf(vx))),
+                   fmaxf(fmaxf(fabsf(vy), fabsf(vz)), fmaxf(fmaxf(fabsf(wx), fabsf(wy)), fabsf(wz)))) + eta;
+  float eb = kOrientCf * perm + 20.0f * eta * mm * mm;
+  if (!(perm > 1e-30f && perm < 1e30f)) return 0;
+  return det > eb ? 1 : (det < -eb ? -1 : 0);
+}
+
+__device__ __forceinline__ int insphere_f(const PtF& a, const PtF& b, const PtF& c, const PtF& d, const PtF& e,
+                                          float eta) {
+  float bx, by, bz, cx, cy, cz, dx, dy, dz, ex, ey, ez;
+  diff_f(b, a, bx, by, bz);
+  diff_f(c, a, cx, cy, cz);
+  diff_f(d, a, dx, dy, dz);
+  diff_f(e, a, ex, ey, ez);
+  float Lb = bx * bx + by * by + bz * bz, Lc = cx * cx + cy * cy + cz * cz;
+  float Ld = dx * dx + dy * dy + dz * dz, Le = ex * ex + ey * ey + ez * ez;
+  // 3x3 minors of the x,y,z columns and their permanents
+  float cd0 = cy * dz - cz * dy, cd1 = cx * dz - cz * dx, cd2 = cx * dy - cy * dx;
+  float pcd0 = fabsf(cy * dz) + fabsf(cz * dy), pcd1 = fabsf(cx * dz) + fabsf(cz * dx),
+        pcd2 = fabsf(cx * dy) + fabsf(cy * dx);
+  float ce0 = cy * ez - cz * ey, ce1 = cx * ez - cz * ex, ce2 = cx * ey - cy * ex;
+  float pce0 = fabsf(cy * ez) + fabsf(cz * ey), pce1 = fabsf(cx * ez) + fabsf(cz * ex),
+        pce2 = fabsf(cx * ey) + fabsf(cy * ex);
+  float de0 = dy * ez - dz * ey, de1 = dx * ez - dz * ex, de2 = dx * ey - dy * ex;
+  float pde0 = fabsf(dy * ez) + fabsf(dz * ey), pde1 = fabsf(dx * ez) + fabsf(dz * ex),
+        pde2 = fabsf(dx * ey) + fabsf(dy * ex);
+  float M0 = cx * de0 - cy * de1 + cz * de2;  // rows c, d, e
+  float M1 = bx * de0 - by * de1 + bz * de2;  // rows b, d, e
+  float M2 = bx * ce0 - by * ce1 + bz * ce2;  // rows b, c, e
+  float M3 = bx * cd0 - by * cd1 + bz * cd2;  // rows b, c, d
+  float P0 = fabsf(cx) * pde0 + fabsf(cy) * pde1 + fabsf(cz) * pde2;
+  float P1 = fabsf(bx) * pde0 + fabsf(by) * pde1 + fabsf(bz) * pde2;
+  float P2 = fabsf(bx) * pce0 + fabsf(by) * pce1 + fabsf(bz) * pce2;
+  float P3 = fabsf(bx) * pcd0 + fabsf(by) * pcd1 + fabsf(bz) * pcd2;
+  float det = (Lc * M1 - Lb * M0) + (Le * M3 - Ld * M2);
+  float perm = (Lc * P1 + Lb * P0) + (Le * P3 + Ld * P2);
+  float mm = fmaxf(fmaxf(fmaxf(fabsf(bx), fabsf(by)), fmaxf(fabsf(bz), fabsf(cx))),
+                   fmaxf(fmaxf(fabsf(cy), fabsf(cz)), fmaxf(fabsf(dx), fabsf(dy))));
+  mm = fmaxf(mm, fmaxf(fmaxf(fabsf(dz), fabsf(ex)), fmaxf(fabsf(ey), fabsf(ez)))) + eta;
+  float mm2 = mm * mm;
+  float eb = kInsphereCf * perm + 400.0f * eta * (mm2 * mm2);
+  if (!(perm > 1e-30f && perm < 1e30f)) return 0;
+  return det > eb ? 1 : (det < -eb ? -1 : 0);
+}
+
 // ----------------------------------------------------------------- filtered predicates
 __device__ __forceinline__ double absmax3(double a, double b, double c) {
   return fmax(fmax(fabs(a), fabs(b)), fabs(c));

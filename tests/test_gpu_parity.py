@@ -61,11 +61,40 @@ def test_device_predicates_match_oracle():
     o = dt.eval_predicates(0, pt).cpu().numpy()
     s = dt.eval_predicates(1, pt).cpu().numpy()
     q = dt.eval_predicates(2, pt, it).cpu().numpy()
+    o32 = dt.eval_predicates(3, pt).cpu().numpy()
+    q32 = dt.eval_predicates(4, pt, it).cpu().numpy()
     for i in range(n):
-        assert o[i] == oracle.orient3d(*p[i, :4]), i
+        ref_o = oracle.orient3d(*p[i, :4])
+        assert o[i] == ref_o and o32[i] == ref_o, i
         assert s[i] == oracle.insphere(*p[i]), i
-        if oracle.orient3d(*p[i, :4]) > 0:
-            assert q[i] == oracle.insphere_sos(p[i], ids[i]), i
+        if ref_o > 0:
+            ref_q = oracle.insphere_sos(p[i], ids[i])
+            assert q[i] == ref_q and q32[i] == ref_q, i
+
+
+def test_fp32_stage_on_nearly_cospherical_tuples():
+    """Points a few ulps off a common sphere, at several scales and offsets: the FP32 stage
+    must either be right or defer, never return a wrong sign."""
+    rng = np.random.default_rng(17)
+    n = 20000
+    p = np.empty((n, 5, 3))
+    for i in range(n):
+        scale = 10.0 ** rng.uniform(-6, 0)
+        off = rng.uniform(-1e3, 1e3, 3) * (rng.random() < 0.3)
+        d = rng.normal(size=(5, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        p[i] = off + scale * d
+        k = rng.integers(0, 15)
+        p[i].flat[k] = np.nextafter(p[i].flat[k], np.inf if rng.random() < 0.5 else -np.inf)
+    ids = np.stack([rng.permutation(100)[:5] for _ in range(n)]).astype(np.int64)
+    pt = torch.from_numpy(p).cuda()
+    o32 = dt.eval_predicates(3, pt).cpu().numpy()
+    q32 = dt.eval_predicates(4, pt, torch.from_numpy(ids).cuda()).cpu().numpy()
+    for i in range(n):
+        ref_o = oracle.orient3d(*p[i, :4])
+        assert o32[i] == ref_o, i
+        if ref_o > 0:
+            assert q32[i] == oracle.insphere_sos(p[i], ids[i]), i
 
 
 # ----------------------------------------------------------------------------- order

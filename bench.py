@@ -206,7 +206,6 @@ def main():
     for _ in range(args.warmup):
         tri.clear()
         tri.insert(xd)
-    ntet = tri.num_tets()
     torch.cuda.synchronize()
 
     def barrier():
@@ -240,6 +239,7 @@ def main():
         t_end.record(stream)
         barrier()
     clocks = clk.summary()
+    ntet = tri.num_tets()
     ms = sum(step_ms) / len(step_ms)
     mine = np.array([sum(step_ms), float(ntet)], dtype=np.float64)
     if dist is not None:

@@ -15,6 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdt_gb300.so")
+RUNNER = os.path.join(BUILD, "dt_run")
 SOURCES = ["order.cu", "dt.cu"]
 HEADERS = ["common.cuh", "predicates.cuh", "engine.cuh", "internal.h"]
 
@@ -72,6 +73,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
         os.replace(tmp, LIB)
+    drv = os.path.join(CSRC, "dt_run.cu")
+    if force or _stale(RUNNER, [drv, LIB]):
+        cmd = [nvcc, *NVCC_FLAGS, "-o", RUNNER + ".tmp", drv, "-L", BUILD, "-ldt_gb300",
+               "-Xlinker", "-rpath=$ORIGIN"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("dt_run build failed:\n" + r.stdout + r.stderr)
+        os.replace(RUNNER + ".tmp", RUNNER)
     return LIB
 
 

@@ -897,9 +897,9 @@ int reserve_tets(dt_handle* h, uint64_t total_pts) {
   if (need <= h->cap_tets) return DT_OK;
   unsigned long long bump = h->has_mesh ? h->st_host->bump : 0;
   if (grow(h->tets, bump, need, h->stream) != cudaSuccess) return DT_ENOMEM;
-  if (grow(h->claim, bump, need, h->stream) != cudaSuccess) return DT_ENOMEM;
+  if (grow(h->claim, 2 * bump, 2 * need, h->stream) != cudaSuccess) return DT_ENOMEM;
   // claim words of slots not yet handed out start at zero (below every priority)
-  cudaMemsetAsync(h->claim + bump, 0, (need - bump) * sizeof(unsigned long long), h->stream);
+  cudaMemsetAsync(h->claim + 2 * bump, 0, 2 * (need - bump) * sizeof(unsigned long long), h->stream);
   uint64_t nf = need / 4 + 4096;
   uint64_t fold = h->has_mesh ? h->st_host->free_avail : 0;
   if (grow(h->freelist, fold, nf, h->stream) != cudaSuccess) return DT_ENOMEM;
@@ -1004,7 +1004,11 @@ int run_big(dt_handle* h, const Ctx& c) {
   uint64_t nbig = h->st_host->q[kQBig];
   int guard = 0;
   while (nbig > 0) {
-    if (++guard > 100000) return DT_ELIMIT;
+    if (++guard > 100000) {
+      h->last_dev_error = 101;  // host-side: large-cavity rounds stopped progressing
+      h->last_dev_info = (unsigned)nbig;
+      return DT_ELIMIT;
+    }
     int rc = set_queue_lengths(h, {kQBig2});
     if (rc != DT_OK) return rc;
     uint32_t R = (uint32_t)std::min<uint64_t>(nbig, kBigR);
@@ -1064,6 +1068,7 @@ int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint
       h->stats.n_profiled++;
     }
   }
+  // large cavities of the pass: inserting them now keeps the remaining neighbourhoods small
   return run_big(h, c);
 }
 
@@ -1126,16 +1131,25 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint
   uint32_t pass = 0;
   int stalled = 0;
   while (nq > 0) {
-    if (h->stats.n_rounds > max_rounds) return DT_ELIMIT;
-    uint64_t before = h->st_host->n_inserted + h->st_host->n_dups;
+    if (h->stats.n_rounds > max_rounds) {
+      h->last_dev_error = 103;  // host-side: round budget exhausted
+      return DT_ELIMIT;
+    }
+    uint64_t before = nq;
     transformed_keys(h->pts, h->queue[kQNext], nq, h->bbox_dev, h->cfg.seed + 0x51ED2701ull * (pass + 1) + vbegin,
                      h->ows.k0, h->ows.v0, s);
-    bool a2 = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, nq, 64, h->ows.hist, s);
+    // the top 24 bits of the 63-bit key (8 levels of the curve) order the retries well enough
+    bool a2 = radix_sort_pairs_bits(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, nq, 39, 63, h->ows.hist, s);
     if ((rc = run_pass(h, c, a2 ? h->ows.v1 : h->ows.v0, 0, nq, true)) != DT_OK) return rc;
     nq = h->st_host->q[kQNext];
-    // a pass that inserted nothing three times in a row is a bug, not a schedule
-    stalled = (h->st_host->n_inserted + h->st_host->n_dups == before) ? stalled + 1 : 0;
-    if (stalled >= 3) return DT_ELIMIT;
+    // every pass shrinks the retry list (its highest-priority located point is inserted, or
+    // moves to the large-cavity queue); three passes that do not are a bug, not a schedule
+    stalled = (nq >= before) ? stalled + 1 : 0;
+    if (stalled >= 3) {
+      h->last_dev_error = 102;  // host-side: retry passes stopped progressing
+      h->last_dev_info = (unsigned)((nq << 8) | (pass & 255));
+      return DT_ELIMIT;
+    }
     ++pass;
   }
   return DT_OK;

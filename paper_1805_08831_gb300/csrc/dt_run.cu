@@ -1,0 +1,63 @@
+// dt_run: command-line driver of the C ABI for profiling (no Python).
+//   dt_run N [steps] [seed]
+// Triangulates N points i.i.d. uniform in the unit cube (SplitMix64 stream, the same recipe as
+// the package's synthetic generator) `steps` times on one handle and prints the tetrahedron
+// count, the device time of each step and the handle's counters.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "../../include/dt.h"
+
+static uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int main(int argc, char** argv) {
+  uint64_t n = argc > 1 ? (uint64_t)std::atof(argv[1]) : 1000000;
+  int steps = argc > 2 ? std::atoi(argv[2]) : 1;
+  uint64_t seed = argc > 3 ? std::strtoull(argv[3], nullptr, 10) : 2;
+  std::vector<double> xyz(3 * n);
+  uint64_t base = seed << 32;
+  for (uint64_t i = 0; i < 3 * n; ++i)
+    xyz[i] = (double)(mix64(base + (i + 1) * 0x9E3779B97F4A7C15ull) >> 11) * (1.0 / 9007199254740992.0);
+  double* d = nullptr;
+  if (cudaMalloc(&d, 24 * n) != cudaSuccess) return 2;
+  cudaMemcpy(d, xyz.data(), 24 * n, cudaMemcpyHostToDevice);
+  dt_config cfg{};
+  cfg.seed = seed;
+  dt_handle* h = nullptr;
+  int rc = dt_create(&h, &cfg);
+  if (rc) return 3;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int s = 0; s < steps; ++s) {
+    dt_clear(h);
+    cudaEventRecord(e0);
+    rc = dt_insert(h, d, n);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    uint64_t T = 0;
+    dt_get_tets(h, nullptr, 0, &T, nullptr, 0);
+    std::printf("step %d rc %d ms %.2f tets %llu Mtets/s %.2f\n", s, rc, ms, (unsigned long long)T, T / ms / 1e3);
+    if (rc) break;
+  }
+  dt_stats st{};
+  dt_get_stats(h, &st);
+  std::printf("rounds %llu passes %llu attempts %llu conflicts %llu launches %llu\n",
+              (unsigned long long)st.n_rounds, (unsigned long long)st.n_passes,
+              (unsigned long long)st.n_attempts, (unsigned long long)st.n_conflicts,
+              (unsigned long long)st.n_launches);
+  dt_destroy(h);
+  cudaFree(d);
+  return rc ? 1 : 0;
+}

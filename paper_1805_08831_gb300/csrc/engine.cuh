@@ -6,11 +6,14 @@
 //   1. walk (thread per point): visibility walk with orient3d (Section 2.1, ghost rules of
 //      Section 2.6) to a tetrahedron in conflict with p;
 //   2. cavity (warp per point): breadth-first search over tetrahedra in conflict (perturbed
-//      insphere, composite ghost sphere), recording the cavity C and its boundary facets; every
-//      tetrahedron of C and of its outside neighbours A is claimed with atomicMax of a
-//      priority (round stamp << 32 | point id + 1);
-//   3. insert (warp per point): a point whose claims on C and A all survived owns them
-//      (rules (1a)(1b) of Section 3.2: winners' C u A sets are disjoint) and replaces C by
+//      insphere, composite ghost sphere), recording the cavity C and its boundary facets. Each
+//      tetrahedron has two claim words, X (priorities of points that delete or touch it) and
+//      Y (priorities of points that delete it); a point with priority (round stamp << 32 |
+//      point id + 1) raises X and Y on its cavity C and X on its outside neighbours A;
+//   3. insert (warp per point): a point wins when X == its priority on all of C and Y is below
+//      its priority on all of A. Then no other winner deletes or touches its C and no other
+//      winner deletes its A (rules (1a)(1b) of Section 3.2); two winners may share outside
+//      tetrahedra, each rewriting a different facet slot. The winner replaces C by
 //      the ball B (Section 2.5): one tetrahedron per boundary facet, the cavity tetrahedron
 //      with its vertex opposite the facet replaced by p, adjacency to the outside tetrahedron
 //      known a priori, adjacencies between new tetrahedra through the n x n edge table of
@@ -39,7 +42,7 @@ constexpr int kHash = 256;  // visited-set slots per warp (shared-memory path)
 
 struct Ctx {
   Tet* tets;
-  unsigned long long* claim;
+  unsigned long long* claim;  // claim[2t] = X, claim[2t + 1] = Y of tetrahedron t
   const Pt* pts;   // exact coordinates; .w = input index (the perturbation order)
   const PtF* ptf;  // double-float copy for the FP32 first stage of the predicates
   float eta;       // absolute error of a double-float difference (see predicates.cuh)
@@ -324,7 +327,8 @@ __device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uint32_t p
     if (!in_conflict(c, t0, p, FP)) flag |= 4;
     w.clist[0] = t0;
     ws_insert(w, t0, 1);
-    if (atomicMax(&c.claim[t0], prio) > prio) flag |= 1;
+    if (atomicMax(&c.claim[2 * (size_t)t0], prio) > prio) flag |= 1;
+    atomicMax(&c.claim[2 * (size_t)t0 + 1], prio);
   }
   flag = __shfl_sync(kFull, flag, 0);
   if (flag & 4) {
@@ -355,7 +359,13 @@ __device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uint32_t p
     int res = 0, myflag = 0;
     if (is_leader) {
       res = in_conflict(c, u, p, FP) ? 1 : 2;
-      if (atomicMax(&c.claim[u], prio) > prio) myflag |= 1;
+      unsigned long long oldx = atomicMax(&c.claim[2 * (size_t)u], prio);
+      if (res == 1) {
+        if (oldx > prio) myflag |= 1;  // a higher priority deletes or touches a tetrahedron of C
+        atomicMax(&c.claim[2 * (size_t)u + 1], prio);
+      } else if (__ldcg(&c.claim[2 * (size_t)u + 1]) > prio) {
+        myflag |= 1;  // a higher priority deletes this outside tetrahedron
+      }
       if (!ws_insert(w, u, (uint8_t)res)) myflag |= 2;
     }
     int lres = __shfl_sync(kFull, res, leader);
@@ -434,7 +444,7 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
   const int lane = threadIdx.x & 31;
   bool ok = true;
   for (int i = lane; i < nc; i += 32)
-    if (__ldcg(&c.claim[clist[i]]) != prio) ok = false;
+    if (__ldcg(&c.claim[2 * (size_t)clist[i]]) != prio) ok = false;
   if (!__all_sync(kFull, ok)) return kCandLost;
   for (int i = lane; i < nb; i += 32) {
     uint32_t e = blist[i];
@@ -447,7 +457,7 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
       ok = false;
       out = 0;
     }
-    if (__ldcg(&c.claim[out >> 2]) != prio) ok = false;
+    if (__ldcg(&c.claim[2 * (size_t)(out >> 2) + 1]) >= prio) ok = false;
     uint4 v = T.v;
     set4(v, f, p);
     w.nv[i] = v;

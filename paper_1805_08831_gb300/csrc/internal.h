@@ -43,6 +43,9 @@ int order_points(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cuda
 // (k, v) and (ka, va); returns true when the sorted result ended in (ka, va).
 bool radix_sort_pairs(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int bits,
                       uint32_t* hist, cudaStream_t s);
+// The same on bits [lo_bit, hi_bit) only (a stable sort by those bits).
+bool radix_sort_pairs_bits(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int lo_bit,
+                           int hi_bit, uint32_t* hist, cudaStream_t s);
 uint64_t radix_hist_entries(uint64_t n);
 
 // Cumulative end of BRIO round r (Section 2.3 / Table 2): 2048 * 7^r.

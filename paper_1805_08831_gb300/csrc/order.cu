@@ -406,11 +406,16 @@ uint64_t radix_hist_entries(uint64_t n) {
 
 bool radix_sort_pairs(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int bits,
                       uint32_t* hist, cudaStream_t s) {
+  return radix_sort_pairs_bits(k, v, ka, va, n, 0, bits, hist, s);
+}
+
+bool radix_sort_pairs_bits(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int lo_bit,
+                           int hi_bit, uint32_t* hist, cudaStream_t s) {
   if (n <= 1) return false;
   uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
   uint64_t len = 256ull * ntiles;
   bool alt = false;
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = lo_bit; shift < hi_bit; shift += 8) {
     uint64_t* sk = alt ? ka : k;
     uint32_t* sv = alt ? va : v;
     uint64_t* dk = alt ? k : ka;

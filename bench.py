@@ -299,7 +299,9 @@ def main():
                    "baseline_ref": "paper Fig. 9, AMD EPYC 7551, 1e7 uniform: 31.3 Mtets/s",
                    "stats": {k: stat_acc[k] for k in ("n_rounds", "n_passes", "n_attempts",
                                                       "n_conflicts", "n_big", "n_exact", "n_sos",
-                                                      "sum_walk", "max_walk", "n_walk_limit")},
+                                                      "sum_walk", "max_walk", "n_walk_limit",
+                                                      "n_rounds_wave", "n_rounds_retry", "n_rounds_big",
+                                                      "ms_first_round")},
                    "mean_C": cfb["C"], "mean_F": cfb["F"],
                    "ms_sort": stat_acc["ms_sort"], "ms_insert": stat_acc["ms_insert"]},
         "e2e": {"value": e2e_value, "unit": "Mtets/s", "h2d_bytes_per_step": n * 24,

@@ -87,6 +87,10 @@ typedef struct {
   uint64_t n_profiled;    /* launches of each round kernel that were timed */
   uint64_t device_error;  /* first device-side error code of the last failing call (0 = none) */
   uint64_t device_error_info;
+  uint64_t n_rounds_wave;  /* rounds of the waves of BRIO rounds */
+  uint64_t n_rounds_retry; /* rounds of the retry passes */
+  uint64_t n_rounds_big;   /* large-cavity rounds */
+  double ms_first_round;   /* device time of the one-block engine (first BRIO round, last call) */
   uint64_t reserved[4];
 } dt_stats;
 

@@ -48,12 +48,15 @@ class Stats(ctypes.Structure):
                    ("n_launches", ctypes.c_uint64), ("ms_walk", ctypes.c_double),
                    ("ms_cavity", ctypes.c_double), ("ms_insert_k", ctypes.c_double),
                    ("n_profiled", ctypes.c_uint64), ("device_error", ctypes.c_uint64),
-                   ("device_error_info", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 4)])
+                   ("device_error_info", ctypes.c_uint64), ("n_rounds_wave", ctypes.c_uint64),
+                   ("n_rounds_retry", ctypes.c_uint64), ("n_rounds_big", ctypes.c_uint64),
+                   ("ms_first_round", ctypes.c_double), ("reserved", ctypes.c_uint64 * 4)])
 
     def as_dict(self):
         d = {f: getattr(self, f) for f in _STAT_FIELDS}
         for f in ("ms_sort", "ms_insert", "n_launches", "ms_walk", "ms_cavity", "ms_insert_k",
-                  "n_profiled", "device_error", "device_error_info"):
+                  "n_profiled", "device_error", "device_error_info", "n_rounds_wave",
+                  "n_rounds_retry", "n_rounds_big", "ms_first_round"):
             d[f] = getattr(self, f)
         d["n_walk_limit"] = self.reserved[0]
         d["free_slots"] = self.reserved[1]

@@ -396,53 +396,64 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
 
 // ------------------------------------------------------------------ one-block engine
 // The first insertions of a cloud (a few thousand points into a mesh that starts with one
-// tetrahedron) offer little parallelism and many conflicts: here one thread block runs whole
-// passes itself, with block barriers in place of kernel boundaries between the walk, cavity
-// and ball phases of a round (up to kCtaWarps concurrent insertions). Large cavities go to the
-// large-cavity queue for the grid path.
+// tetrahedron) offer little parallelism and large cavities: one thread block runs all of the
+// first BRIO round itself, with block barriers in place of kernel boundaries between the walk,
+// cavity and ball phases of a round. It takes the round's waves in order (up to kCtaWarps
+// concurrent insertions, alpha * mesh size), then retries the points that lost until none is
+// left. Each warp works in its own global-memory workspace, so cavities of up to
+// kCtaCN / kCtaFN tetrahedra / facets stay here; larger ones go to the serial path.
 constexpr int kCtaWarps = 16;
+constexpr uint32_t kCtaHashN = 2048, kCtaCN = 512, kCtaFN = 512, kCtaEdgeN = 2048;
 
-struct CtaWarpSmem {
-  uint4 nv[kFMax];
-  uint4 nn[kFMax];
-  uint32_t hkey[kHash];
-  uint32_t clist[kCMax];
-  uint32_t blist[kFMax];
-  uint32_t outh[kFMax];
-  uint32_t slot[kFMax];
-  uint32_t vkey[32];
-  uint16_t tab[32 * 32];
-  uint8_t hval[kHash];
-  uint8_t ipos[kFMax + 4];
-};
+inline size_t cta_stride() { return carve(nullptr, kCtaHashN, kCtaCN, kCtaFN, kCtaEdgeN, nullptr); }
 
-__global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, uint32_t vbegin, uint32_t m0,
+__global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, const uint32_t* __restrict__ wlist,
+                                                               const uint32_t* __restrict__ cum, int nwaves,
                                                                const uint8_t* __restrict__ vflag,
                                                                uint32_t* list_a, uint32_t* list_b,
-                                                               uint32_t* big_out, float alpha,
-                                                               uint32_t max_passes) {
-  extern __shared__ __align__(16) unsigned char cta_smem[];
-  CtaWarpSmem* ws = reinterpret_cast<CtaWarpSmem*>(cta_smem);
+                                                               uint32_t* huge_out, char* wsmem, size_t wsstride,
+                                                               float alpha, uint32_t max_passes) {
   __shared__ uint32_t s_p[kCtaWarps], s_t[kCtaWarps], s_st[kCtaWarps], s_nc[kCtaWarps], s_nb[kCtaWarps];
   __shared__ unsigned int s_nout, s_R, s_err;
   __shared__ unsigned long long s_L, s_N0;
   __shared__ unsigned long long s_stat[6];  // inserted, conflicts, attempts, cavity, ball, walk
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const uint32_t* q = nullptr;
-  uint32_t* out = list_a;
-  uint64_t m = m0;
+  BigWS ws;
+  carve(wsmem + (size_t)wid * wsstride, kCtaHashN, kCtaCN, kCtaFN, kCtaEdgeN, &ws);
   if (tid < 6) s_stat[tid] = 0;
-  if (tid == 0) s_N0 = __ldcg(&c.st->n_inserted);
+  if (tid == 0) {
+    s_N0 = __ldcg(&c.st->n_inserted);
+    s_nout = 0;
+  }
   __syncthreads();
-  for (uint32_t pass = 0; m > 0 && pass < max_passes; ++pass) {
+  // passes: the waves (in order), then retries of the points that lost
+  const uint32_t* q = wlist;
+  uint64_t m = 0;
+  uint32_t* out = list_a;
+  int wave = 0;
+  uint64_t woff = 0;
+  for (uint32_t pass = 0; pass < max_passes; ++pass) {
+    if (wave < nwaves) {
+      q = wlist + woff;
+      m = cum[wave] - woff;
+      woff = cum[wave];
+      ++wave;
+    } else {
+      // all waves done: the points that lost during them (or during the last retry)
+      q = out;
+      m = s_nout;
+      out = (out == list_a) ? list_b : list_a;
+      __syncthreads();
+      if (tid == 0) s_nout = 0;
+      if (m == 0) break;
+    }
     if (tid == 0) {
       double N = (double)(s_N0 + s_stat[0]);
       uint64_t R = (uint64_t)fmax(1.0, alpha * N);
       R = R > kCtaWarps ? kCtaWarps : R;
       R = R > m ? m : R;
-      s_R = (unsigned)R;
-      s_L = (m + R - 1) / R;
-      s_nout = 0;
+      s_R = (unsigned)(R > 0 ? R : 1);
+      s_L = (m + s_R - 1) / s_R;
       s_err = __ldcg(&c.st->error);
     }
     __syncthreads();
@@ -455,11 +466,11 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, uint32_t v
         uint64_t idx = (uint64_t)tid * L + j;
         uint32_t status = kCandEmpty, p = kNone, t = kNone;
         if (idx < m) {
-          p = q ? q[idx] : vbegin + (uint32_t)idx;
+          p = q[idx];
           if (vflag[p] == 0) {
             PtF FP = load_ptf(c.ptf, p);
             uint32_t hint = c.point_hint[p];
-            if (hint == kNone && j > 0) hint = c.point_hint[q ? q[idx - 1] : vbegin + (uint32_t)(idx - 1)];
+            if (hint == kNone && j > 0) hint = c.point_hint[q[idx - 1]];
             if (hint == kNone) {
               uint32_t f, g;
               cells_of(c, FP, &f, &g);
@@ -477,35 +488,32 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, uint32_t v
         s_st[tid] = status;
       }
       __syncthreads();
-      // cavity: one warp per candidate
+      // cavity: one warp per candidate, in its own workspace
       if (wid < (int)R && s_st[wid] == kCandLocated) {
         uint32_t p = s_p[wid];
         unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
-        CtaWarpSmem& w = ws[wid];
-        CavWS cw{w.hkey, w.hval, kHash - 1, w.clist, kCMax, w.blist, kFMax};
         int nc = 0, nb = 0;
-        int r = cavity_warp(c, cw, s_t[wid], p, load_ptf(c.ptf, p), prio, &nc, &nb);
+        int r = cavity_warp(c, ws.cav, s_t[wid], p, load_ptf(c.ptf, p), prio, &nc, &nb);
         if (lane == 0) {
           s_st[wid] = (uint32_t)r;
           s_nc[wid] = (uint32_t)nc;
           s_nb[wid] = (uint32_t)nb;
         }
       }
+      __threadfence();
       __syncthreads();
-      // ball: the same warp, from its shared-memory cavity
+      // ball: the same warp, from its workspace
       if (wid < (int)R && s_st[wid] == kCandLocated) {
         uint32_t p = s_p[wid];
         unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
-        CtaWarpSmem& w = ws[wid];
-        InsWS iw{w.nv, w.nn, w.outh, w.slot, w.ipos, w.vkey, w.tab, nullptr, nullptr, nullptr, nullptr, 0};
         int nc = (int)s_nc[wid], nb = (int)s_nb[wid];
-        int r = insert_warp(c, iw, p, prio, w.clist, nc, w.blist, nb, true, __ldcg(&c.st->free_avail),
-                            __ldcg(&c.st->bump), c.st->capacity);
+        int r = insert_warp(c, ws.ins, p, prio, ws.cav.clist, nc, ws.cav.blist, nb, nb <= kFMax,
+                            __ldcg(&c.st->free_avail), __ldcg(&c.st->bump), c.st->capacity);
         if (lane == 0) {
           s_st[wid] = (uint32_t)r;
           if (r == kCandInserted) {
             PtF FP = load_ptf(c.ptf, p);
-            uint32_t f, g, s0 = w.slot[0];
+            uint32_t f, g, s0 = ws.ins.slot[0];
             cells_of(c, FP, &f, &g);
             c.cell_hint[f] = s0;
             c.cell_hint2[g] = s0;
@@ -524,16 +532,11 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, uint32_t v
         if (st != kCandEmpty) atomicAdd(&s_stat[2], 1ull);
         if (st == kCandLost) atomicAdd(&s_stat[1], 1ull);
         if (st == kCandLost || st == kCandWalkLimit) out[atomicAdd(&s_nout, 1u)] = p;
-        else if (st == kCandBig) big_out[atomicAdd(&c.st->q[kQBig], 1ull)] = p;
+        else if (st == kCandBig) huge_out[atomicAdd(&c.st->q[kQHuge], 1ull)] = p;
         else if (st == kCandDup) atomicAdd(&c.st->n_dups, 1ull);
       }
       finish_round_block(c);
     }
-    __syncthreads();
-    // the points of this pass that did not make it are the next pass
-    q = out;
-    m = s_nout;
-    out = (out == list_a) ? list_b : list_a;
     __syncthreads();
   }
   if (tid == 0) {
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, uint32_t v
     atomicAdd(&c.st->sum_cavity, s_stat[3]);
     atomicAdd(&c.st->sum_ball, s_stat[4]);
     atomicAdd(&c.st->sum_walk, s_stat[5]);
-    if (m > 0) raise_error(c.st, kErrInternal, 0xF000u);
+    if (s_nout > 0 || wave < nwaves) raise_error(c.st, kErrInternal, 0xF000u);
   }
 }
 
@@ -807,6 +810,8 @@ struct dt_handle {
   char* bigmem = nullptr;   // kBigR large-cavity workspaces
   size_t bigstride = 0;
   char* hugemem = nullptr;  // the serial path's workspace
+  char* ctamem = nullptr;   // the one-block engine's per-warp workspaces
+  size_t ctastride = 0;
   BigWS hugews{};
   double* bbox_dev = nullptr;
   bool has_mesh = false;
@@ -817,7 +822,7 @@ struct dt_handle {
   uint32_t* wlist = nullptr;
   uint32_t* wave_cum = nullptr;
   uint64_t cap_w = 0;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> prof_events;
   unsigned long long next_stamp = 1;
   unsigned long long launches0 = 0;
@@ -925,6 +930,8 @@ int reserve_rounds(dt_handle* h, uint64_t qcap) {
       return DT_ENOMEM;
     h->bigstride = big_stride();
     if (cudaMalloc(&h->bigmem, h->bigstride * kBigR)) return DT_ENOMEM;
+    h->ctastride = cta_stride();
+    if (cudaMalloc(&h->ctamem, h->ctastride * kCtaWarps)) return DT_ENOMEM;
     size_t huge = carve(nullptr, kHugeHash, kHugeC, kHugeF, kHugeEdge, nullptr);
     if (cudaMalloc(&h->hugemem, huge)) return DT_ENOMEM;
     carve(h->hugemem, kHugeHash, kHugeC, kHugeF, kHugeEdge, &h->hugews);
@@ -989,6 +996,7 @@ void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, bool big, uint6
   ++g_kernel_launches;
   if (prof) cudaEventRecord(h->prof_events[6 * j_prof + 5], s);
   h->stats.n_rounds++;
+  if (big) h->stats.n_rounds_big++;
 }
 
 int set_queue_lengths(dt_handle* h, std::initializer_list<int> which) {
@@ -1036,6 +1044,7 @@ int run_big(dt_handle* h, const Ctx& c) {
 // One pass: rounds over q[0..m) (or the vertex range qbase + [0, m)) split into R segments of
 // length L (segment s offers q[s*L + j] in round j), then the large cavities of the pass.
 int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next) {
+  uint64_t& kind_rounds = reset_next ? h->stats.n_rounds_retry : h->stats.n_rounds_wave;
   uint64_t mesh = h->st_host->n_inserted;
   uint32_t R = choose_segments(h, mesh, m);
   uint64_t L = (m + R - 1) / R;
@@ -1053,6 +1062,7 @@ int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint
     RoundIO io{q, qbase, m, L, j, R, h->queue[kQNext], kQNext, h->queue[kQBig], kQBig};
     launch_round(h, c, io, false, j);
   }
+  kind_rounds += L;
   h->stats.n_passes++;
   if ((rc = sync_state(h)) != DT_OK) return rc;
   if (cudaGetLastError() != cudaSuccess) return DT_ECUDA;
@@ -1072,22 +1082,54 @@ int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint
   return run_big(h, c);
 }
 
+// Waves of one BRIO round (see run_brio_round): fills h->wlist with the round's vertices grouped
+// by wave, Moore order inside each wave, h->wave_cum with the cumulative wave ends, and returns
+// the number of waves.
+int make_waves(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint64_t base, std::vector<uint32_t>& cum) {
+  cudaStream_t s = h->stream;
+  uint64_t m = vend - vbegin;
+  cum.clear();
+  double N = (double)std::max<uint64_t>(h->st_host->n_inserted, 4);
+  uint64_t acc = 0;
+  while (acc < m && cum.size() < 255) {
+    uint64_t w = (uint64_t)std::max(1.0, std::ceil(h->gamma * N));
+    acc = std::min<uint64_t>(m, acc + w);
+    cum.push_back((uint32_t)acc);
+    N += (double)w;
+  }
+  cum.back() = (uint32_t)m;
+  if (cudaMemcpyAsync(h->wave_cum, cum.data(), cum.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return -1;
+  uint64_t rank0 = round == 0 ? 0 : brio_round_end(round - 1);
+  k_wave_keys<<<grid_for(m, 256), 256, 0, s>>>(vbegin, m, base, rank0, h->ows.perm, h->ows.rank, h->wave_cum,
+                                                (int)cum.size(), h->ows.k0, h->ows.v0);
+  ++g_kernel_launches;
+  bool alt = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, m, 8, h->ows.hist, s);
+  cudaMemcpyAsync(h->wlist, alt ? h->ows.v1 : h->ows.v0, m * 4, cudaMemcpyDeviceToDevice, s);
+  return (int)cum.size();
+}
+
 // The first BRIO round of a new triangulation on one thread block (see k_cta_insert).
-int run_cta_round(dt_handle* h, uint32_t vbegin, uint32_t vend) {
+int run_cta_round(dt_handle* h, uint32_t vbegin, uint32_t vend, uint64_t base) {
   Ctx c = make_ctx(h);
   Ctx cc = c;
   cc.coherent = 1;
   int rc = set_queue_lengths(h, {kQBig, kQHuge});
   if (rc != DT_OK) return rc;
-  size_t smem = sizeof(CtaWarpSmem) * kCtaWarps;
-  if (cudaFuncSetAttribute(k_cta_insert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return DT_ECUDA;
-  k_cta_insert<<<1, kCtaWarps * 32, smem, h->stream>>>(cc, vbegin, vend - vbegin, h->vflag, h->queue[kQNext],
-                                                        h->queue[kQBig2], h->queue[kQBig], (float)h->alpha_cta,
-                                                        1u << 16);
+  std::vector<uint32_t> cum;
+  int nw = make_waves(h, vbegin, vend, 0, base, cum);
+  if (nw < 0) return DT_ECUDA;
+  cudaEventRecord(h->ev[3], h->stream);
+  k_cta_insert<<<1, kCtaWarps * 32, 0, h->stream>>>(cc, h->wlist, h->wave_cum, nw, h->vflag, h->queue[kQNext],
+                                                     h->queue[kQBig2], h->queue[kQHuge], h->ctamem, h->ctastride,
+                                                     (float)h->alpha_cta, 1u << 16);
   ++g_kernel_launches;
+  cudaEventRecord(h->ev[4], h->stream);
   h->stats.n_passes++;
   if ((rc = sync_state(h)) != DT_OK) return rc;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]);
+  h->stats.ms_first_round = ms;
   return run_big(h, c);
 }
 
@@ -1101,25 +1143,8 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint
   cudaStream_t s = h->stream;
   uint64_t m = vend - vbegin;
   uint32_t max_rounds = h->cfg.max_rounds ? h->cfg.max_rounds : (1u << 22);
-  // wave boundaries (cumulative ranks inside the round)
   std::vector<uint32_t> cum;
-  double N = (double)std::max<uint64_t>(h->st_host->n_inserted, 4);
-  uint64_t acc = 0;
-  while (acc < m && cum.size() < 255) {
-    uint64_t w = (uint64_t)std::max(1.0, std::ceil(h->gamma * N));
-    acc = std::min<uint64_t>(m, acc + w);
-    cum.push_back((uint32_t)acc);
-    N += (double)w;
-  }
-  cum.back() = (uint32_t)m;
-  if (cudaMemcpyAsync(h->wave_cum, cum.data(), cum.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return DT_ECUDA;
-  uint64_t rank0 = round == 0 ? 0 : brio_round_end(round - 1);
-  k_wave_keys<<<grid_for(m, 256), 256, 0, s>>>(vbegin, m, base, rank0, h->ows.perm, h->ows.rank, h->wave_cum,
-                                                (int)cum.size(), h->ows.k0, h->ows.v0);
-  ++g_kernel_launches;
-  bool alt = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, m, 8, h->ows.hist, s);
-  cudaMemcpyAsync(h->wlist, alt ? h->ows.v1 : h->ows.v0, m * 4, cudaMemcpyDeviceToDevice, s);
+  if (make_waves(h, vbegin, vend, round, base, cum) < 0) return DT_ECUDA;
   int rc = set_queue_lengths(h, {kQNext});
   if (rc != DT_OK) return rc;
   uint64_t off = 0;
@@ -1215,7 +1240,7 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
     if (b >= n) break;
     uint64_t e = std::min<uint64_t>(brio_round_end(r), n);
     if (r == 0 && h->st_host->n_inserted <= 4 && !std::getenv("DT_NO_CTA"))
-      rc = run_cta_round(h, (uint32_t)(base + b), (uint32_t)(base + e));
+      rc = run_cta_round(h, (uint32_t)(base + b), (uint32_t)(base + e), base);
     else
       rc = run_brio_round(h, (uint32_t)(base + b), (uint32_t)(base + e), r, base);
     if (rc != DT_OK) return rc;
@@ -1470,6 +1495,7 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->wave_cum);
   cudaFree(h->bigmem);
   cudaFree(h->hugemem);
+  cudaFree(h->ctamem);
   cudaFree(h->bbox_dev);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);

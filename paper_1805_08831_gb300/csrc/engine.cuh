@@ -290,11 +290,18 @@ __device__ bool in_conflict(const Ctx& c, uint32_t u, uint32_t p, const PtF& FP)
 // ------------------------------------------------------------------ visited set
 __device__ __forceinline__ uint32_t hash32(uint32_t k) { return k * 0x9E3779B1u; }
 
+// Workspace arrays may live in global memory, where another lane's atomic or store is not
+// seen through this SM's L1: lanes read each other's entries with volatile loads.
+template <class T>
+__device__ __forceinline__ T vld(const T* p) {
+  return *reinterpret_cast<const volatile T*>(p);
+}
+
 __device__ __forceinline__ int ws_find(const CavWS& w, uint32_t key) {
   uint32_t h = (hash32(key) >> 8) & w.hmask;
   for (uint32_t probe = 0; probe <= w.hmask; ++probe) {
-    uint32_t k = w.hkey[h];
-    if (k == key) return w.hval[h];
+    uint32_t k = vld(&w.hkey[h]);
+    if (k == key) return vld(&w.hval[h]);
     if (k == kNone) return 0;
     h = (h + 1) & w.hmask;
   }
@@ -343,7 +350,7 @@ __device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uint32_t p
     bool active = k < batch;
     uint32_t t = 0, u = kNone;
     if (active) {
-      t = w.clist[head + k];
+      t = vld(&w.clist[head + k]);
       u = nbr_at(c, t, f) >> 2;
       if (u >= c.ntets) {
         raise_error(c.st, kErrInternal, 0xC000u);
@@ -444,10 +451,10 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
   const int lane = threadIdx.x & 31;
   bool ok = true;
   for (int i = lane; i < nc; i += 32)
-    if (__ldcg(&c.claim[2 * (size_t)clist[i]]) != prio) ok = false;
+    if (__ldcg(&c.claim[2 * (size_t)vld(&clist[i])]) != prio) ok = false;
   if (!__all_sync(kFull, ok)) return kCandLost;
   for (int i = lane; i < nb; i += 32) {
-    uint32_t e = blist[i];
+    uint32_t e = vld(&blist[i]);
     uint32_t t = e >> 2;
     int f = (int)(e & 3u);
     Tet T = load_tet_cg(c.tets, t);
@@ -472,7 +479,7 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
   base = __shfl_sync(kFull, base, 0);
   bool fail = false;
   for (int i = lane; i < nb; i += 32)
-    w.slot[i] = (i < reuse) ? clist[i] : virtual_slot(c, base + (unsigned long long)(i - reuse), fa, bump, cap, fail);
+    w.slot[i] = (i < reuse) ? vld(&clist[i]) : virtual_slot(c, base + (unsigned long long)(i - reuse), fa, bump, cap, fail);
   if (__any_sync(kFull, fail)) {
     if (lane == 0) raise_error(c.st, kErrCapacity, (unsigned)nb);
     return kCandLost;
@@ -539,14 +546,14 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
     uint32_t ea, eb, ec;
     if (use_table) {
       int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
-      ea = w.tab[lc * 32 + lb];
-      eb = w.tab[la * 32 + lc];
-      ec = w.tab[lb * 32 + la];
+      ea = vld(&w.tab[lc * 32 + lb]);
+      eb = vld(&w.tab[la * 32 + lc]);
+      ec = vld(&w.tab[lb * 32 + la]);
     } else {
       uint32_t hh[3];
       for (int k = 0; k < 3; ++k) {
         uint32_t old = w.hold[3 * i + k];
-        hh[k] = (old != kNone) ? old : w.eval[w.hslot[3 * i + k]];
+        hh[k] = (old != kNone) ? old : vld(&w.eval[w.hslot[3 * i + k]]);
       }
       ea = hh[0];
       eb = hh[1];
@@ -559,9 +566,9 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
     }
     uint4 nn;
     set4(nn, ip, w.outh[i]);
-    set4(nn, a, 4u * w.slot[ea >> 2] + (ea & 3u));
-    set4(nn, b, 4u * w.slot[eb >> 2] + (eb & 3u));
-    set4(nn, cc, 4u * w.slot[ec >> 2] + (ec & 3u));
+    set4(nn, a, 4u * vld(&w.slot[ea >> 2]) + (ea & 3u));
+    set4(nn, b, 4u * vld(&w.slot[eb >> 2]) + (eb & 3u));
+    set4(nn, cc, 4u * vld(&w.slot[ec >> 2]) + (ec & 3u));
     w.nn[i] = nn;
   }
   if (__any_sync(kFull, bad)) {
@@ -584,9 +591,9 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
     unsigned long long pb = 0;
     if (lane == 0) pb = atomicAdd(&c.st->pending, (unsigned long long)freed);
     pb = __shfl_sync(kFull, pb, 0);
-    uint32_t redirect = w.slot[0];
+    uint32_t redirect = vld(&w.slot[0]);
     for (int i = lane; i < freed; i += 32) {
-      uint32_t s = clist[nb + i];
+      uint32_t s = vld(&clist[nb + i]);
       uint4* dst = reinterpret_cast<uint4*>(c.tets + s);
       dst[0] = make_uint4(kDeadMark, kDeadMark, kDeadMark, kDeadMark);
       dst[1] = make_uint4(redirect, kNone, kNone, kNone);

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c, RoundIO io, const uint8_t* 
 }
 
 template <bool kBig>
-__global__ void __launch_bounds__(256) k_cavity(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
+__global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
                                                 const uint32_t* __restrict__ cand_t, uint32_t* cand_status,
                                                 uint32_t* cand_nc, uint32_t* cand_nb, uint32_t* scratch,
                                                 char* bigmem, size_t bigstride) {
@@ -210,6 +210,36 @@ __device__ void finish_round_block(const Ctx& c) {
   __syncthreads();
 }
 
+// Closes a round run by a single warp (the serial path, and the last warp of the insert kernel).
+__device__ void finish_round_warp(const Ctx& c) {
+  const int lane = threadIdx.x & 31;
+  DevState* st = c.st;
+  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
+  unsigned long long np = __ldcg(&st->pending);
+  __syncwarp();
+  unsigned long long consumed = used < fa ? used : fa;
+  unsigned long long nfa = fa - consumed;
+  if (nfa + np > st->free_capacity) {
+    if (lane == 0) raise_error(st, kErrFreeList, 0);
+    np = st->free_capacity - nfa;
+  }
+  for (unsigned long long i = lane; i < np; i += 32) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
+  __syncwarp();
+  if (lane == 0) {
+    st->bump += used - consumed;
+    st->free_avail = nfa + np;
+    st->alloc_cursor = 0;
+    st->pending = 0;
+    st->stamp += 1;
+    st->blocks_done = 0;
+  }
+  __threadfence();
+  __syncwarp();
+}
+
+// Ball phase: each warp verifies and inserts one candidate independently (no block barrier);
+// the last warp of each block flushes the block's counters, and the last of those closes the
+// round.
 template <bool kBig>
 __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_t* __restrict__ cand_p,
                                                 uint32_t* cand_status, const uint32_t* __restrict__ cand_nc,
@@ -224,12 +254,13 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
   __shared__ uint8_t s_ipos[W][kFMax + 4];
   __shared__ uint32_t s_vkey[W][32];
   __shared__ uint16_t s_tab[W][32 * 32];
-  __shared__ unsigned int s_nq, s_nbig, s_last;
-  __shared__ unsigned long long s_qbase, s_bbase;
+  __shared__ unsigned int s_warps_done, s_nlose, s_nbigq;
+  __shared__ uint32_t s_lose[kWarps], s_bigq[kWarps];
   __shared__ unsigned long long s_stat[6];  // inserted, conflicts, attempts, cavity, ball, dups
   if (threadIdx.x == 0) {
-    s_nq = 0;
-    s_nbig = 0;
+    s_warps_done = 0;
+    s_nlose = 0;
+    s_nbigq = 0;
     for (int k = 0; k < 6; ++k) s_stat[k] = 0;
   }
   __syncthreads();
@@ -273,64 +304,51 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
       atomicAdd(&s_stat[4], (unsigned long long)nb);
     }
   }
-  int qslot = -1, bslot = -1;
-  if (lane == 0 && cand < io.R && status != kCandEmpty) {
-    atomicAdd(&s_stat[2], 1ull);
-    if (status == kCandLost) atomicAdd(&s_stat[1], 1ull);
-    if (status == kCandDup) atomicAdd(&s_stat[5], 1ull);
-    if (status == kCandLost || status == kCandWalkLimit) qslot = (int)atomicAdd(&s_nq, 1u);
-    else if (status == kCandBig) bslot = (int)atomicAdd(&s_nbig, 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    s_qbase = s_nq ? atomicAdd(&c.st->q[io.lose_q], (unsigned long long)s_nq) : 0;
-    s_bbase = s_nbig ? atomicAdd(&c.st->q[io.big_q], (unsigned long long)s_nbig) : 0;
-    if (s_stat[0]) atomicAdd(&c.st->n_inserted, s_stat[0]);
-    if (s_stat[1]) atomicAdd(&c.st->n_conflicts, s_stat[1]);
-    if (s_stat[2]) atomicAdd(&c.st->n_attempts, s_stat[2]);
-    if (s_stat[3]) atomicAdd(&c.st->sum_cavity, s_stat[3]);
-    if (s_stat[4]) atomicAdd(&c.st->sum_ball, s_stat[4]);
-    if (s_stat[5]) atomicAdd(&c.st->n_dups, s_stat[5]);
-    if (kBig && s_stat[0]) atomicAdd(&c.st->n_big, s_stat[0]);
-  }
-  __syncthreads();
-  if (qslot >= 0) io.lose_out[s_qbase + qslot] = p;
-  if (bslot >= 0) io.big_out[s_bbase + bslot] = p;
-  // the last block to finish closes the round
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&c.st->blocks_done, 1u) == gridDim.x - 1) ? 1u : 0u;
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    finish_round_block(c);
-  }
-}
-
-// Closes a round run by a single warp (the serial path).
-__device__ void finish_round_warp(const Ctx& c) {
-  const int lane = threadIdx.x & 31;
-  DevState* st = c.st;
-  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
-  unsigned long long np = __ldcg(&st->pending);
-  __syncwarp();
-  unsigned long long consumed = used < fa ? used : fa;
-  unsigned long long nfa = fa - consumed;
-  if (nfa + np > st->free_capacity) {
-    if (lane == 0) raise_error(st, kErrFreeList, 0);
-    np = st->free_capacity - nfa;
-  }
-  for (unsigned long long i = lane; i < np; i += 32) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
-  __syncwarp();
+  unsigned int closer = 0;
   if (lane == 0) {
-    st->bump += used - consumed;
-    st->free_avail = nfa + np;
-    st->alloc_cursor = 0;
-    st->pending = 0;
-    st->stamp += 1;
+    if (cand < io.R && status != kCandEmpty) {
+      atomicAdd(&s_stat[2], 1ull);
+      if (status == kCandLost) atomicAdd(&s_stat[1], 1ull);
+      if (status == kCandDup) atomicAdd(&s_stat[5], 1ull);
+      if (status == kCandLost || status == kCandWalkLimit) s_lose[atomicAdd(&s_nlose, 1u)] = p;
+      else if (status == kCandBig) s_bigq[atomicAdd(&s_nbigq, 1u)] = p;
+    }
+    __threadfence_block();
+    if (atomicAdd(&s_warps_done, 1u) == kWarps - 1) {
+      // every warp of the block has counted itself: flush the block's queues and counters
+      closer = 1;
+      unsigned nl = s_nlose, nbq = s_nbigq;
+      if (nl) {
+        unsigned long long b = atomicAdd(&c.st->q[io.lose_q], (unsigned long long)nl);
+        for (unsigned k = 0; k < nl; ++k) io.lose_out[b + k] = s_lose[k];
+      }
+      if (nbq) {
+        unsigned long long b = atomicAdd(&c.st->q[io.big_q], (unsigned long long)nbq);
+        for (unsigned k = 0; k < nbq; ++k) io.big_out[b + k] = s_bigq[k];
+      }
+      if (s_stat[0]) atomicAdd(&c.st->n_inserted, s_stat[0]);
+      if (s_stat[1]) atomicAdd(&c.st->n_conflicts, s_stat[1]);
+      if (s_stat[2]) atomicAdd(&c.st->n_attempts, s_stat[2]);
+      if (s_stat[3]) atomicAdd(&c.st->sum_cavity, s_stat[3]);
+      if (s_stat[4]) atomicAdd(&c.st->sum_ball, s_stat[4]);
+      if (s_stat[5]) atomicAdd(&c.st->n_dups, s_stat[5]);
+      if (kBig && s_stat[0]) atomicAdd(&c.st->n_big, s_stat[0]);
+    }
   }
-  __threadfence();
-  __syncwarp();
+  // the last warp of the last block closes the round
+  closer = __shfl_sync(kFull, closer, 0);
+  if (closer == 1u) {
+    unsigned int last = 0;
+    if (lane == 0) {
+      __threadfence();
+      last = (atomicAdd(&c.st->blocks_done, 1u) == gridDim.x - 1) ? 1u : 0u;
+    }
+    last = __shfl_sync(kFull, last, 0);
+    if (last) {
+      __threadfence();
+      finish_round_warp(c);
+    }
+  }
 }
 
 // Points whose cavity exceeds even the large-cavity workspaces: inserted one at a time by one
@@ -402,7 +420,7 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
 // concurrent insertions, alpha * mesh size), then retries the points that lost until none is
 // left. Each warp works in its own global-memory workspace, so cavities of up to
 // kCtaCN / kCtaFN tetrahedra / facets stay here; larger ones go to the serial path.
-constexpr int kCtaWarps = 16;
+constexpr int kCtaWarps = 32;
 constexpr uint32_t kCtaHashN = 2048, kCtaCN = 512, kCtaFN = 512, kCtaEdgeN = 2048;
 
 inline size_t cta_stride() { return carve(nullptr, kCtaHashN, kCtaCN, kCtaFN, kCtaEdgeN, nullptr); }
@@ -865,7 +883,9 @@ Ctx make_ctx(dt_handle* h) {
     c.sc[k] = h->sc[k];
   }
   c.cb = h->cb;
-  c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : (1u << 16);
+  // a walk that has not arrived after this many steps continues in the next pass, from where it
+  // stopped, so one long walk does not hold up a whole round
+  c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : 96u;
   c.coherent = 0;
   c.ntets = (uint32_t)h->cap_tets;
   c.npts = (uint32_t)h->cap_pts;

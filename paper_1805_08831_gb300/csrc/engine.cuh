@@ -600,6 +600,7 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
       if (pb + i < c.st->free_capacity) c.pending[pb + i] = s;
       else raise_error(c.st, kErrFreeList, 0);
     }
+    __threadfence();  // the warp that closes the round reads these entries
   }
   return kCandInserted;
 }

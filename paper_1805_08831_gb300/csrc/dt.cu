@@ -18,6 +18,8 @@ namespace dtg {
 namespace {
 
 constexpr int kWarps = 8;  // candidates per 256-thread block in the warp-per-point kernels
+constexpr uint64_t kLongWalkBelow = 8192;      // retry lists shorter than this walk up to
+constexpr uint32_t kLongWalkSteps = 1u << 14;  // this many steps per pass
 constexpr uint32_t kScratchStride = kCMax + kFMax;
 
 // Queues of points a round hands on (DevState::q).
@@ -66,7 +68,7 @@ __host__ __device__ inline size_t carve(char* base, uint32_t hashn, uint32_t cn,
   x.ins.outh = (uint32_t*)take((size_t)fn * 4);
   x.ins.slot = (uint32_t*)take((size_t)fn * 4);
   x.ins.vkey = (uint32_t*)take(32 * 4);
-  x.ins.tab = (uint16_t*)take(32 * 32 * 2);
+  x.ins.tab = (uint8_t*)take(32 * 32);
   x.cav.hval = (uint8_t*)take(hashn);
   x.ins.ipos = (uint8_t*)take(fn);
   x.cav.hmask = hashn - 1;
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
   __shared__ uint32_t s_slot[W][kFMax];
   __shared__ uint8_t s_ipos[W][kFMax + 4];
   __shared__ uint32_t s_vkey[W][32];
-  __shared__ uint16_t s_tab[W][32 * 32];
+  __shared__ uint8_t s_tab[W][32 * 32];
   __shared__ unsigned int s_warps_done, s_nlose, s_nbigq;
   __shared__ uint32_t s_lose[kWarps], s_bigq[kWarps];
   __shared__ unsigned long long s_stat[6];  // inserted, conflicts, attempts, cavity, ball, dups
@@ -837,6 +839,7 @@ struct dt_handle {
   double alpha = 0.03;   // candidates per round = alpha * mesh vertices
   double gamma = 0.3;    // wave size = gamma * mesh vertices
   double alpha_cta = 0.1;  // candidates per round of the one-block engine (at most 16)
+  int walk_threads = 64;   // block size of the thread-per-point walk: small blocks spread a round over every SM
   uint32_t* wlist = nullptr;
   uint32_t* wave_cum = nullptr;
   uint64_t cap_w = 0;
@@ -879,8 +882,8 @@ Ctx make_ctx(dt_handle* h) {
   c.point_hint = h->point_hint;
   c.st = h->st;
   for (int k = 0; k < 3; ++k) {
-    c.lo[k] = h->lo[k];
-    c.sc[k] = h->sc[k];
+    c.lo[k] = (float)h->lo[k];
+    c.sc[k] = (float)h->sc[k];
   }
   c.cb = h->cb;
   // a walk that has not arrived after this many steps continues in the next pass, from where it
@@ -989,7 +992,8 @@ void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, bool big, uint6
   cudaStream_t s = h->stream;
   uint32_t R = io.R;
   if (prof) cudaEventRecord(h->prof_events[6 * j_prof], s);
-  k_walk<<<(R + 255) / 256, 256, 0, s>>>(c, io, h->vflag, h->cand_p, h->cand_t, h->cand_status);
+  const unsigned wt = (unsigned)h->walk_threads;
+  k_walk<<<(R + wt - 1) / wt, wt, 0, s>>>(c, io, h->vflag, h->cand_p, h->cand_t, h->cand_status);
   ++g_kernel_launches;
   if (prof) {
     cudaEventRecord(h->prof_events[6 * j_prof + 1], s);
@@ -1180,16 +1184,21 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint
       h->last_dev_error = 103;  // host-side: round budget exhausted
       return DT_ELIMIT;
     }
-    uint64_t before = nq;
+    uint64_t before = nq, limited = h->st_host->n_walk_limit;
     transformed_keys(h->pts, h->queue[kQNext], nq, h->bbox_dev, h->cfg.seed + 0x51ED2701ull * (pass + 1) + vbegin,
                      h->ows.k0, h->ows.v0, s);
     // the top 24 bits of the 63-bit key (8 levels of the curve) order the retries well enough
     bool a2 = radix_sort_pairs_bits(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, nq, 39, 63, h->ows.hist, s);
-    if ((rc = run_pass(h, c, a2 ? h->ows.v1 : h->ows.v0, 0, nq, true)) != DT_OK) return rc;
+    // a short retry list is cheap per round: let its walks run long instead of over many passes
+    Ctx cr = c;
+    if (!h->cfg.max_walk_steps && nq < kLongWalkBelow) cr.max_walk = kLongWalkSteps;
+    if ((rc = run_pass(h, cr, a2 ? h->ows.v1 : h->ows.v0, 0, nq, true)) != DT_OK) return rc;
     nq = h->st_host->q[kQNext];
     // every pass shrinks the retry list (its highest-priority located point is inserted, or
-    // moves to the large-cavity queue); three passes that do not are a bug, not a schedule
-    stalled = (nq >= before) ? stalled + 1 : 0;
+    // moves to the large-cavity queue) or advances walks that hit their step limit; three
+    // passes that do neither are a bug, not a schedule
+    bool walking = h->st_host->n_walk_limit > limited;
+    stalled = (nq >= before && !walking) ? stalled + 1 : 0;
     if (stalled >= 3) {
       h->last_dev_error = 102;  // host-side: retry passes stopped progressing
       h->last_dev_info = (unsigned)((nq << 8) | (pass & 255));
@@ -1320,6 +1329,10 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (const char* a = std::getenv("DT_ALPHA")) h->alpha = std::atof(a);
   if (const char* g = std::getenv("DT_GAMMA")) h->gamma = std::atof(g);
   if (const char* a = std::getenv("DT_ALPHA_CTA")) h->alpha_cta = std::atof(a);
+  if (const char* w = std::getenv("DT_WALK_THREADS")) {
+    int v = std::atoi(w);
+    if (v == 32 || v == 64 || v == 128 || v == 256) h->walk_threads = v;
+  }
   bool ok = cudaMalloc(&h->st, sizeof(DevState)) == cudaSuccess &&
             cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess;
   for (auto& e : h->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;

@@ -52,7 +52,7 @@ struct Ctx {
   uint32_t* cell_hint2;   // coarse grid (8 x 8 x 8 fine cells per coarse cell)
   uint32_t* point_hint;   // per vertex: where its last walk ended / its ball
   DevState* st;
-  double lo[3], sc[3];
+  float lo[3], sc[3];  // hint grid: cell = floor((x - lo) * sc), clamped (a hint, not exact)
   int cb;  // bits per axis of the hint grid
   uint32_t max_walk;
   int coherent;  // 1 when this kernel also writes the tetrahedra it reads (L2 loads)
@@ -100,7 +100,7 @@ struct InsWS {
   uint32_t* slot;
   uint8_t* ipos;
   uint32_t* vkey;  // 32-slot vertex hash: slot = cavity-local vertex index
-  uint16_t* tab;   // 32 x 32 edge table
+  uint8_t* tab;    // 32 x 32 edge table: 4 * (new tetrahedron) + facet, below 4 * kFMax
   unsigned long long* ekey;
   uint32_t* eval;
   uint32_t* hslot;
@@ -118,12 +118,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Fine and coarse hint-grid cells of P.
 __device__ __forceinline__ void cells_of(const Ctx& c, const PtF& P, uint32_t* fine, uint32_t* coarse) {
-  double x[3] = {(double)P.hx, (double)P.hy, (double)P.hz};
-  double lim = (double)((1u << c.cb) - 1u);
+  const float x[3] = {P.hx, P.hy, P.hz};
+  const float lim = (float)((1u << c.cb) - 1u);
   uint32_t q[3];
   for (int k = 0; k < 3; ++k) {
-    double f = floor((x[k] - c.lo[k]) * c.sc[k]);
-    f = f < 0.0 ? 0.0 : (f > lim ? lim : f);
+    float f = floorf((x[k] - c.lo[k]) * c.sc[k]);
+    f = f < 0.0f ? 0.0f : (f > lim ? lim : f);  // also maps NaN to 0
     q[k] = (uint32_t)f;
   }
   *fine = (q[2] << (2 * c.cb)) | (q[1] << c.cb) | q[0];
@@ -144,10 +144,17 @@ __device__ __forceinline__ Pt sel4(int i, int k, Pt P, Pt V) { return i == k ? P
 
 // ------------------------------------------------------------------ walk (Section 2.1)
 __device__ __forceinline__ const PtF& self4(int i, int k, const PtF& P, const PtF& V) { return i == k ? P : V; }
-__device__ __forceinline__ Pt self4d(int i, int k, const Pt& P, const Pt& V) { return i == k ? P : V; }
 
 __device__ __forceinline__ bool same_f(const PtF& a, const PtF& b) {
   return a.hx == b.hx && a.hy == b.hy && a.hz == b.hz && a.lx == b.lx && a.ly == b.ly && a.lz == b.lz;
+}
+
+// FP64 (then exact) orientation with vertex i of v replaced by p, out of line (rarely reached).
+// Vertex i itself is never read: it may be the ghost vertex, which has no coordinates.
+__device__ __noinline__ int orient_replace_fp64(const Ctx& c, uint4 v, int i, uint32_t p) {
+  Pt r[4];
+  for (int k = 0; k < 4; ++k) r[k] = load_pt(c.pts, k == i ? p : get4(v, k));
+  return orient3d(r[0], r[1], r[2], r[3], c.st);
 }
 
 // orient3d of tetrahedron vertices v[] with vertex i replaced by the query p (FP32 stage first).
@@ -155,9 +162,7 @@ __device__ __forceinline__ int orient_replace(const Ctx& c, const uint4& v, int 
                                               const PtF& F0, const PtF& F1, const PtF& F2, const PtF& F3) {
   int o = orient3d_f(self4(i, 0, FP, F0), self4(i, 1, FP, F1), self4(i, 2, FP, F2), self4(i, 3, FP, F3), c.eta);
   if (o != 0) return o;
-  Pt P = load_pt(c.pts, p);
-  Pt V0 = load_pt(c.pts, v.x), V1 = load_pt(c.pts, v.y), V2 = load_pt(c.pts, v.z), V3 = load_pt(c.pts, v.w);
-  return orient3d(self4d(i, 0, P, V0), self4d(i, 1, P, V1), self4d(i, 2, P, V2), self4d(i, 3, P, V3), c.st);
+  return orient_replace_fp64(c, v, i, p);
 }
 
 // Returns kCandLocated (*t_out in conflict with p), kCandWalkLimit (*t_out = where it stopped)
@@ -250,12 +255,18 @@ __device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32_t star
 
 // ------------------------------------------------------------------ conflict test
 // Perturbed insphere of a finite tetrahedron and p: negative = p inside (FP32 stage first).
+// FP64 (then exact, then perturbed) insphere, out of line: the FP32 stage settles nearly every
+// test, and keeping this path out of the callers keeps their registers for the common case.
+__device__ __noinline__ bool inside_finite_fp64(const Ctx& c, uint4 v, uint32_t p) {
+  Pt a = load_pt(c.pts, v.x), b = load_pt(c.pts, v.y), d = load_pt(c.pts, v.z), e = load_pt(c.pts, v.w);
+  return insphere_sos(a, b, d, e, load_pt(c.pts, p), c.st) < 0;
+}
+
 __device__ __forceinline__ bool inside_finite(const Ctx& c, const uint4& v, uint32_t p, const PtF& FP) {
   PtF A = load_ptf(c.ptf, v.x), B = load_ptf(c.ptf, v.y), C = load_ptf(c.ptf, v.z), D = load_ptf(c.ptf, v.w);
   int s = insphere_f(A, B, C, D, FP, c.eta);
   if (s != 0) return s < 0;
-  Pt a = load_pt(c.pts, v.x), b = load_pt(c.pts, v.y), d = load_pt(c.pts, v.z), e = load_pt(c.pts, v.w);
-  return insphere_sos(a, b, d, e, load_pt(c.pts, p), c.st) < 0;
+  return inside_finite_fp64(c, v, p);
 }
 
 // Membership of tetrahedron u in the cavity of p: perturbed insphere for a finite tetrahedron;
@@ -272,11 +283,7 @@ __device__ bool in_conflict(const Ctx& c, uint32_t u, uint32_t p, const PtF& FP)
   PtF q[4];
   for (int k = 0; k < 4; ++k) q[k] = (k == g) ? FP : load_ptf(c.ptf, get4(U.v, k));
   int o = orient3d_f(q[0], q[1], q[2], q[3], c.eta);
-  if (o == 0) {
-    Pt r[4];
-    for (int k = 0; k < 4; ++k) r[k] = load_pt(c.pts, k == g ? p : get4(U.v, k));
-    o = orient3d(r[0], r[1], r[2], r[3], c.st);
-  }
+  if (o == 0) o = orient_replace_fp64(c, U.v, g, p);
   if (o != 0) return o > 0;
   uint32_t rr = get4(U.n, g) >> 2;
   Tet R = tet_at(c, rr);
@@ -504,9 +511,9 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
         vfail = true;
         continue;
       }
-      w.tab[lb * 32 + lc] = (uint16_t)((i << 2) | a);
-      w.tab[lc * 32 + la] = (uint16_t)((i << 2) | b);
-      w.tab[la * 32 + lb] = (uint16_t)((i << 2) | cc);
+      w.tab[lb * 32 + lc] = (uint8_t)((i << 2) | a);
+      w.tab[lc * 32 + la] = (uint8_t)((i << 2) | b);
+      w.tab[la * 32 + lb] = (uint8_t)((i << 2) | cc);
     }
     if (__any_sync(kFull, vfail)) {
       if (lane == 0) raise_error(c.st, kErrInternal, 0x7AB1u);

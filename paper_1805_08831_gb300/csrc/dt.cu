@@ -68,7 +68,7 @@ __host__ __device__ inline size_t carve(char* base, uint32_t hashn, uint32_t cn,
   x.ins.outh = (uint32_t*)take((size_t)fn * 4);
   x.ins.slot = (uint32_t*)take((size_t)fn * 4);
   x.ins.vkey = (uint32_t*)take(32 * 4);
-  x.ins.tab = (uint8_t*)take(32 * 32);
+  x.ins.tab = (uint16_t*)take(32 * 32 * 2);
   x.cav.hval = (uint8_t*)take(hashn);
   x.ins.ipos = (uint8_t*)take(fn);
   x.cav.hmask = hashn - 1;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
   __shared__ uint32_t s_slot[W][kFMax];
   __shared__ uint8_t s_ipos[W][kFMax + 4];
   __shared__ uint32_t s_vkey[W][32];
-  __shared__ uint8_t s_tab[W][32 * 32];
+  __shared__ uint16_t s_tab[W][32 * 32];
   __shared__ unsigned int s_warps_done, s_nlose, s_nbigq;
   __shared__ uint32_t s_lose[kWarps], s_bigq[kWarps];
   __shared__ unsigned long long s_stat[6];  // inserted, conflicts, attempts, cavity, ball, dups

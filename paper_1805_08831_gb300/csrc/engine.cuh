@@ -100,7 +100,7 @@ struct InsWS {
   uint32_t* slot;
   uint8_t* ipos;
   uint32_t* vkey;  // 32-slot vertex hash: slot = cavity-local vertex index
-  uint8_t* tab;    // 32 x 32 edge table: 4 * (new tetrahedron) + facet, below 4 * kFMax
+  uint16_t* tab;   // 32 x 32 edge table: 4 * (new tetrahedron) + facet
   unsigned long long* ekey;
   uint32_t* eval;
   uint32_t* hslot;
@@ -149,20 +149,17 @@ __device__ __forceinline__ bool same_f(const PtF& a, const PtF& b) {
   return a.hx == b.hx && a.hy == b.hy && a.hz == b.hz && a.lx == b.lx && a.ly == b.ly && a.lz == b.lz;
 }
 
-// FP64 (then exact) orientation with vertex i of v replaced by p, out of line (rarely reached).
-// Vertex i itself is never read: it may be the ghost vertex, which has no coordinates.
-__device__ __noinline__ int orient_replace_fp64(const Ctx& c, uint4 v, int i, uint32_t p) {
-  Pt r[4];
-  for (int k = 0; k < 4; ++k) r[k] = load_pt(c.pts, k == i ? p : get4(v, k));
-  return orient3d(r[0], r[1], r[2], r[3], c.st);
-}
+__device__ __forceinline__ Pt self4d(int i, int k, const Pt& P, const Pt& V) { return i == k ? P : V; }
 
 // orient3d of tetrahedron vertices v[] with vertex i replaced by the query p (FP32 stage first).
+// v must be a finite tetrahedron: all four of its vertices are read on the FP64 path.
 __device__ __forceinline__ int orient_replace(const Ctx& c, const uint4& v, int i, uint32_t p, const PtF& FP,
                                               const PtF& F0, const PtF& F1, const PtF& F2, const PtF& F3) {
   int o = orient3d_f(self4(i, 0, FP, F0), self4(i, 1, FP, F1), self4(i, 2, FP, F2), self4(i, 3, FP, F3), c.eta);
   if (o != 0) return o;
-  return orient_replace_fp64(c, v, i, p);
+  Pt P = load_pt(c.pts, p);
+  Pt V0 = load_pt(c.pts, v.x), V1 = load_pt(c.pts, v.y), V2 = load_pt(c.pts, v.z), V3 = load_pt(c.pts, v.w);
+  return orient3d(self4d(i, 0, P, V0), self4d(i, 1, P, V1), self4d(i, 2, P, V2), self4d(i, 3, P, V3), c.st);
 }
 
 // Returns kCandLocated (*t_out in conflict with p), kCandWalkLimit (*t_out = where it stopped)
@@ -283,7 +280,11 @@ __device__ bool in_conflict(const Ctx& c, uint32_t u, uint32_t p, const PtF& FP)
   PtF q[4];
   for (int k = 0; k < 4; ++k) q[k] = (k == g) ? FP : load_ptf(c.ptf, get4(U.v, k));
   int o = orient3d_f(q[0], q[1], q[2], q[3], c.eta);
-  if (o == 0) o = orient_replace_fp64(c, U.v, g, p);
+  if (o == 0) {  // the ghost vertex has no coordinates: only p and the hull facet are read
+    Pt r[4];
+    for (int k = 0; k < 4; ++k) r[k] = load_pt(c.pts, k == g ? p : get4(U.v, k));
+    o = orient3d(r[0], r[1], r[2], r[3], c.st);
+  }
   if (o != 0) return o > 0;
   uint32_t rr = get4(U.n, g) >> 2;
   Tet R = tet_at(c, rr);
@@ -511,9 +512,9 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
         vfail = true;
         continue;
       }
-      w.tab[lb * 32 + lc] = (uint8_t)((i << 2) | a);
-      w.tab[lc * 32 + la] = (uint8_t)((i << 2) | b);
-      w.tab[la * 32 + lb] = (uint8_t)((i << 2) | cc);
+      w.tab[lb * 32 + lc] = (uint16_t)((i << 2) | a);
+      w.tab[lc * 32 + la] = (uint16_t)((i << 2) | b);
+      w.tab[la * 32 + lb] = (uint16_t)((i << 2) | cc);
     }
     if (__any_sync(kFull, vfail)) {
       if (lane == 0) raise_error(c.st, kErrInternal, 0x7AB1u);

@@ -91,6 +91,13 @@ typedef struct {
   uint64_t n_rounds_retry; /* rounds of the retry passes */
   uint64_t n_rounds_big;   /* large-cavity rounds */
   double ms_first_round;   /* device time of the one-block engine (first BRIO round, last call) */
+  uint64_t n_walk_limit;   /* walks stopped at max_walk_steps (each resumes in a later pass) */
+  uint64_t free_slots;     /* slots on the free list after the last round */
+  uint64_t max_walk;       /* longest single walk (steps) */
+  uint64_t n_clouds_degenerate; /* dt_batch: clouds with fewer than four non-coplanar points */
+  uint64_t batch_warps;    /* dt_batch: block shape used (warps per block, autotuned) */
+  double batch_alpha;      /* dt_batch: concurrent insertions per mesh vertex used (autotuned) */
+  double ms_batch_tune;    /* dt_batch: host time of the autotuning in the last call (0 = reused) */
   uint64_t reserved[4];
 } dt_stats;
 
@@ -112,10 +119,20 @@ int dt_insert(dt_handle* h, const double* xyz_dev, uint64_t n);
 /* Same as dt_insert, with host input: the points are copied to the device inside the call. */
 int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n);
 
-/* Triangulates n_clouds independent clouds in one persistent launch (one cooperative thread
- * block per cloud at a time). xyz_dev holds the clouds back to back ([sum n_i, 3], device);
- * offsets_host[c] .. offsets_host[c+1] delimit cloud c (host array of n_clouds + 1 entries,
- * offsets_host[0] = 0). Replaces the handle's content. Vertex ids are local to each cloud. */
+/* Triangulates n_clouds independent clouds: one batched sort (each cloud gets its own box,
+ * Moore keys, duplicates and BRIO rounds, exactly as dt_insert would give it alone), then ONE
+ * persistent kernel launch in which every thread block takes whole clouds from a device work
+ * counter (largest first) and runs Algorithm 1 for all of a cloud's points with its warps
+ * inserting concurrently (the Section 3.2 conflict rules between them). The block shape (warps
+ * per block) and the round size are chosen by an autotuner that times candidates on a sample of
+ * the clouds the first time a batch of this kind (cloud count, size range) is seen.
+ *  - xyz_dev: the clouds back to back, [sum n_i, 3] float64 (device);
+ *  - offsets_host: n_clouds + 1 ascending entries (host), offsets_host[0] = 0; cloud c is rows
+ *    offsets_host[c] .. offsets_host[c + 1].
+ * Replaces the handle's content (dt_insert returns DT_ESTATE until dt_clear). A cloud with fewer
+ * than four non-coplanar points gets no tetrahedra and is counted in n_clouds_degenerate; the
+ * call returns DT_EDEGENERATE only if every cloud is so. Vertex ids in dt_get_tets are local to
+ * each cloud. Each cloud's tetrahedra are those of dt_insert on that cloud alone. */
 int dt_batch(dt_handle* h, const double* xyz_dev, const uint64_t* offsets_host, uint32_t n_clouds);
 
 /* Copies the finite tetrahedra of the current triangulation into tets_dev ([cap, 4] uint32,

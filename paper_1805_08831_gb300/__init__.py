@@ -50,17 +50,19 @@ class Stats(ctypes.Structure):
                    ("n_profiled", ctypes.c_uint64), ("device_error", ctypes.c_uint64),
                    ("device_error_info", ctypes.c_uint64), ("n_rounds_wave", ctypes.c_uint64),
                    ("n_rounds_retry", ctypes.c_uint64), ("n_rounds_big", ctypes.c_uint64),
-                   ("ms_first_round", ctypes.c_double), ("reserved", ctypes.c_uint64 * 4)])
+                   ("ms_first_round", ctypes.c_double), ("n_walk_limit", ctypes.c_uint64),
+                   ("free_slots", ctypes.c_uint64), ("max_walk", ctypes.c_uint64),
+                   ("n_clouds_degenerate", ctypes.c_uint64), ("batch_warps", ctypes.c_uint64),
+                   ("batch_alpha", ctypes.c_double), ("ms_batch_tune", ctypes.c_double),
+                   ("reserved", ctypes.c_uint64 * 4)])
 
     def as_dict(self):
         d = {f: getattr(self, f) for f in _STAT_FIELDS}
         for f in ("ms_sort", "ms_insert", "n_launches", "ms_walk", "ms_cavity", "ms_insert_k",
                   "n_profiled", "device_error", "device_error_info", "n_rounds_wave",
-                  "n_rounds_retry", "n_rounds_big", "ms_first_round"):
+                  "n_rounds_retry", "n_rounds_big", "ms_first_round", "n_walk_limit", "free_slots",
+                  "max_walk", "n_clouds_degenerate", "batch_warps", "batch_alpha", "ms_batch_tune"):
             d[f] = getattr(self, f)
-        d["n_walk_limit"] = self.reserved[0]
-        d["free_slots"] = self.reserved[1]
-        d["max_walk"] = self.reserved[2]
         return d
 
 
@@ -191,6 +193,36 @@ class Triangulation:
             raise ValueError("xyz must be [n, 3]")
         self._check_dev(lib().dt_insert_host(self._h, a.ctypes.data_as(ctypes.c_void_p), a.shape[0]),
                         "dt_insert_host")
+
+    def batch(self, xyz, offsets):
+        """Triangulates independent clouds in one call: xyz is a CUDA float64 tensor [N, 3] with
+        the clouds back to back, offsets the n_clouds + 1 row offsets (host, offsets[0] = 0)."""
+        torch = _torch()
+        if not (isinstance(xyz, torch.Tensor) and xyz.is_cuda and xyz.dtype == torch.float64):
+            raise TypeError("xyz must be a CUDA float64 tensor [N, 3]")
+        xyz = xyz.contiguous()
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        if off.ndim != 1 or off.size < 2:
+            raise ValueError("offsets must hold n_clouds + 1 entries")
+        self._check_dev(lib().dt_batch(self._h, ctypes.c_void_p(xyz.data_ptr()),
+                                       off.ctypes.data_as(ctypes.c_void_p), off.size - 1), "dt_batch")
+        self._n_clouds = off.size - 1
+
+    def tets_batch(self, canonical: bool = True):
+        """After batch(): (tets numpy uint32 [T, 4] with cloud-local ids, cloud_offsets numpy
+        uint64 [n_clouds + 1]); each cloud's rows are canonical on their own."""
+        torch = _torch()
+        nc = self._n_clouds
+        coff = np.zeros(nc + 1, dtype=np.uint64)
+        n = ctypes.c_uint64()
+        rc = lib().dt_get_tets(self._h, None, 0, ctypes.byref(n), coff.ctypes.data_as(ctypes.c_void_p), 0)
+        if rc not in (DT_OK, DT_ETOOSMALL):
+            _check(rc, "dt_get_tets")
+        T = n.value
+        out = torch.empty((max(T, 1), 4), dtype=torch.int32, device="cuda")
+        _check(lib().dt_get_tets(self._h, ctypes.c_void_p(out.data_ptr()), T, ctypes.byref(n),
+                                 coff.ctypes.data_as(ctypes.c_void_p), 1 if canonical else 0), "dt_get_tets")
+        return out[: n.value].cpu().numpy().view(np.uint32), coff
 
     def num_tets(self) -> int:
         n = ctypes.c_uint64()

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -40,44 +41,6 @@ constexpr uint32_t kHugeHash = 1u << 17;
 constexpr uint32_t kHugeC = 1u << 15;
 constexpr uint32_t kHugeF = 1u << 15;
 constexpr uint32_t kHugeEdge = 1u << 17;
-
-struct BigWS {
-  CavWS cav;
-  InsWS ins;
-};
-
-// Carves the workspaces of one candidate out of a byte range (global memory).
-__host__ __device__ inline size_t carve(char* base, uint32_t hashn, uint32_t cn, uint32_t fn, uint32_t edgen,
-                                        BigWS* w) {
-  size_t off = 0;
-  auto take = [&](size_t n) {
-    char* r = base ? base + off : nullptr;
-    off += (n + 15) & ~size_t(15);
-    return r;
-  };
-  BigWS x{};
-  x.ins.ekey = (unsigned long long*)take((size_t)edgen * 8);
-  x.ins.nv = (uint4*)take((size_t)fn * 16);
-  x.ins.nn = (uint4*)take((size_t)fn * 16);
-  x.cav.hkey = (uint32_t*)take((size_t)hashn * 4);
-  x.cav.clist = (uint32_t*)take((size_t)cn * 4);
-  x.cav.blist = (uint32_t*)take((size_t)fn * 4);
-  x.ins.eval = (uint32_t*)take((size_t)edgen * 4);
-  x.ins.hslot = (uint32_t*)take((size_t)fn * 3 * 4);
-  x.ins.hold = (uint32_t*)take((size_t)fn * 3 * 4);
-  x.ins.outh = (uint32_t*)take((size_t)fn * 4);
-  x.ins.slot = (uint32_t*)take((size_t)fn * 4);
-  x.ins.vkey = (uint32_t*)take(32 * 4);
-  x.ins.tab = (uint16_t*)take(32 * 32 * 2);
-  x.cav.hval = (uint8_t*)take(hashn);
-  x.ins.ipos = (uint8_t*)take(fn);
-  x.cav.hmask = hashn - 1;
-  x.cav.cmax = cn;
-  x.cav.bmax = fn;
-  x.ins.emask = edgen - 1;
-  if (w) *w = x;
-  return off;
-}
 
 inline size_t big_stride() { return carve(nullptr, kBigHashN, kBigCN, kBigFN, kBigEdgeN, nullptr); }
 
@@ -182,61 +145,6 @@ __global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint
     cand_nc[cand] = (uint32_t)nc;
     cand_nb[cand] = (uint32_t)nb;
   }
-}
-
-// Closes a round (run by the last block of the insert kernel): the allocator consumed the top
-// of the free list, then the bump pointer; slots freed during the round join the free list;
-// the claim stamp advances.
-__device__ void finish_round_block(const Ctx& c) {
-  DevState* st = c.st;
-  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
-  unsigned long long np = __ldcg(&st->pending);
-  __syncthreads();
-  unsigned long long consumed = used < fa ? used : fa;
-  unsigned long long nfa = fa - consumed;
-  if (nfa + np > st->free_capacity) {
-    if (threadIdx.x == 0) raise_error(st, kErrFreeList, 0);
-    np = st->free_capacity - nfa;
-  }
-  for (unsigned long long i = threadIdx.x; i < np; i += blockDim.x) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->bump += used - consumed;
-    st->free_avail = nfa + np;
-    st->alloc_cursor = 0;
-    st->pending = 0;
-    st->stamp += 1;
-    st->blocks_done = 0;
-    __threadfence();
-  }
-  __syncthreads();
-}
-
-// Closes a round run by a single warp (the serial path, and the last warp of the insert kernel).
-__device__ void finish_round_warp(const Ctx& c) {
-  const int lane = threadIdx.x & 31;
-  DevState* st = c.st;
-  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
-  unsigned long long np = __ldcg(&st->pending);
-  __syncwarp();
-  unsigned long long consumed = used < fa ? used : fa;
-  unsigned long long nfa = fa - consumed;
-  if (nfa + np > st->free_capacity) {
-    if (lane == 0) raise_error(st, kErrFreeList, 0);
-    np = st->free_capacity - nfa;
-  }
-  for (unsigned long long i = lane; i < np; i += 32) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
-  __syncwarp();
-  if (lane == 0) {
-    st->bump += used - consumed;
-    st->free_avail = nfa + np;
-    st->alloc_cursor = 0;
-    st->pending = 0;
-    st->stamp += 1;
-    st->blocks_done = 0;
-  }
-  __threadfence();
-  __syncwarp();
 }
 
 // Ball phase: each warp verifies and inserts one candidate independently (no block barrier);
@@ -594,76 +502,7 @@ __global__ void k_wave_keys(uint32_t vbegin, uint64_t m, uint64_t base, uint64_t
 // positive tetrahedron; four ghost tetrahedra close it (Section 2.6).
 __global__ void k_init(Ctx c, uint32_t vbegin, uint32_t vend, uint8_t* vflag) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint32_t s = vbegin;
-  while (s < vend && vflag[s]) ++s;
-  uint32_t i0 = s++;
-  while (s < vend && vflag[s]) ++s;
-  uint32_t i1 = s++;
-  if (i1 >= vend) {
-    raise_error(c.st, kErrDegenerate, 0);
-    return;
-  }
-  Pt A = c.pts[i0], B = c.pts[i1];
-  while (s < vend && (vflag[s] || collinear_exact(A, B, c.pts[s], c.st))) ++s;
-  uint32_t i2 = s++;
-  if (i2 >= vend) {
-    raise_error(c.st, kErrDegenerate, 1);
-    return;
-  }
-  Pt C = c.pts[i2];
-  while (s < vend && (vflag[s] || orient3d(A, B, C, c.pts[s], c.st) == 0)) ++s;
-  uint32_t i3 = s;
-  if (i3 >= vend) {
-    raise_error(c.st, kErrDegenerate, 2);
-    return;
-  }
-  uint32_t v[4] = {i0, i1, i2, i3};
-  if (orient3d(A, B, C, c.pts[i3], c.st) < 0) {
-    v[2] = i3;
-    v[3] = i2;
-  }
-  uint32_t tv[5][4];
-  for (int k = 0; k < 4; ++k) tv[0][k] = v[k];
-  for (int i = 0; i < 4; ++i) {
-    for (int k = 0; k < 4; ++k) tv[1 + i][k] = v[k];
-    tv[1 + i][i] = kGhost;
-    int a = (i == 0) ? 1 : 0, b = (i <= 1) ? 2 : 1;
-    uint32_t x = tv[1 + i][a];
-    tv[1 + i][a] = tv[1 + i][b];
-    tv[1 + i][b] = x;
-  }
-  uint32_t nn[5][4];
-  for (int t = 0; t < 5; ++t)
-    for (int f = 0; f < 4; ++f) {
-      nn[t][f] = kNone;
-      for (int u = 0; u < 5 && nn[t][f] == kNone; ++u) {
-        if (u == t) continue;
-        for (int g = 0; g < 4; ++g) {
-          // facet f of t equals facet g of u when the other three vertices coincide as sets
-          int match = 0;
-          for (int a = 0; a < 4; ++a) {
-            if (a == f) continue;
-            for (int b = 0; b < 4; ++b)
-              if (b != g && tv[t][a] == tv[u][b]) {
-                ++match;
-                break;
-              }
-          }
-          if (match == 3) {
-            nn[t][f] = 4u * u + g;
-            break;
-          }
-        }
-      }
-    }
-  for (int t = 0; t < 5; ++t) {
-    c.tets[t].v = make_uint4(tv[t][0], tv[t][1], tv[t][2], tv[t][3]);
-    c.tets[t].n = make_uint4(nn[t][0], nn[t][1], nn[t][2], nn[t][3]);
-  }
-  vflag[i0] = vflag[i1] = vflag[i2] = vflag[i3] = 2;
-  c.st->bump = 5;
-  c.st->anchor = 0;
-  c.st->n_inserted += 4;
+  init_mesh(c, vbegin, vend, vflag, 0);
 }
 
 __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
@@ -700,20 +539,7 @@ __global__ void k_collect(const Tet* __restrict__ tets, uint64_t nslots, const P
     if (tet_dead(v) || ghost_pos(v) >= 0) continue;
     if (v.x >= npts || v.y >= npts || v.z >= npts || v.w >= npts) continue;
     uint32_t r[4] = {(uint32_t)pts[v.x].w, (uint32_t)pts[v.y].w, (uint32_t)pts[v.z].w, (uint32_t)pts[v.w].w};
-    if (canonical) {
-      // even permutation bringing the smallest id first, then a cyclic turn of the other three
-      int k = 0;
-      for (int i = 1; i < 4; ++i)
-        if (r[i] < r[k]) k = i;
-      uint32_t a[4];
-      if (k == 0) { a[0] = r[0]; a[1] = r[1]; a[2] = r[2]; a[3] = r[3]; }
-      else if (k == 1) { a[0] = r[1]; a[1] = r[0]; a[2] = r[3]; a[3] = r[2]; }
-      else if (k == 2) { a[0] = r[2]; a[1] = r[0]; a[2] = r[1]; a[3] = r[3]; }
-      else { a[0] = r[3]; a[1] = r[0]; a[2] = r[2]; a[3] = r[1]; }
-      if (a[2] < a[1] && a[2] < a[3]) { uint32_t x = a[1]; a[1] = a[2]; a[2] = a[3]; a[3] = x; }
-      else if (a[3] < a[1] && a[3] < a[2]) { uint32_t x = a[3]; a[3] = a[2]; a[2] = a[1]; a[1] = x; }
-      for (int i = 0; i < 4; ++i) r[i] = a[i];
-    }
+    if (canonical) canonical_rotation(r);
     unsigned long long pos = atomicAdd(count, 1ull);
     if (pos < cap) {
       reinterpret_cast<uint4*>(out)[pos] = make_uint4(r[0], r[1], r[2], r[3]);
@@ -849,6 +675,32 @@ struct dt_handle {
   unsigned long long launches0 = 0;
   dt_stats stats{};
   unsigned last_dev_error = 0, last_dev_info = 0;
+  // batch of clouds (dt_batch)
+  bool batch_mode = false;
+  uint32_t n_clouds = 0;
+  std::vector<uint64_t> boff;              // input offsets of the clouds
+  std::vector<BatchCloud> bclouds_host;    // per-cloud ranges and results
+  uint64_t* boff_dev = nullptr;
+  BatchCloud* bclouds = nullptr;
+  uint32_t* border = nullptr;               // clouds by decreasing size
+  uint32_t* bsample = nullptr;              // the autotuner's sample of clouds
+  uint64_t cap_bclouds = 0;
+  uint32_t* bcid = nullptr;
+  uint8_t* bdup = nullptr;                  // duplicate flags by vertex (sorted position)
+  uint32_t *blist_a = nullptr, *blist_b = nullptr, *blist_big = nullptr;
+  uint64_t cap_bpts = 0;
+  uint32_t *bhint_f = nullptr, *bhint_c = nullptr;
+  double* bcbox = nullptr;
+  DevState* bstates = nullptr;
+  uint64_t cap_bstates = 0;
+  char* bws = nullptr;
+  size_t cap_bws = 0;
+  unsigned long long* bstats = nullptr;
+  unsigned int* bnext = nullptr;
+  int batch_W = 0;                          // autotuned block shape (warps per block), 0 = not tuned
+  float batch_alpha = 0.f;                  // autotuned concurrent insertions per mesh vertex
+  uint64_t batch_sig = 0;                   // workload signature the tuning belongs to
+  double batch_tune_ms = 0.0;
 };
 
 namespace {
@@ -1286,6 +1138,318 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
   return DT_OK;
 }
 
+// ------------------------------------------------------------------ batches of clouds
+template <class T>
+bool realloc_dev(T*& p, uint64_t n) {
+  cudaFree(p);
+  p = nullptr;
+  return cudaMalloc(&p, std::max<uint64_t>(n, 1) * sizeof(T)) == cudaSuccess;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  return n;
+}
+
+// Device memory of a batch of nc clouds, N points and T tetrahedron slots (in total).
+int batch_reserve(dt_handle* h, uint64_t N, uint32_t nc, uint64_t T) {
+  if (reserve_points(h, N) != DT_OK) return DT_ENOMEM;
+  if (order_ws_reserve(h->ows, N) != cudaSuccess) return DT_ENOMEM;
+  if (N > h->cap_bpts) {
+    if (!realloc_dev(h->bcid, N) || !realloc_dev(h->bdup, N) || !realloc_dev(h->blist_a, N) ||
+        !realloc_dev(h->blist_b, N) || !realloc_dev(h->blist_big, N))
+      return DT_ENOMEM;
+    h->cap_bpts = N;
+  }
+  if (nc > h->cap_bclouds) {
+    if (!realloc_dev(h->boff_dev, (uint64_t)nc + 1) || !realloc_dev(h->bclouds, nc) || !realloc_dev(h->border, nc) ||
+        !realloc_dev(h->bsample, nc) || !realloc_dev(h->bhint_f, (uint64_t)nc * batch_hint_fine()) ||
+        !realloc_dev(h->bhint_c, (uint64_t)nc * batch_hint_coarse()) || !realloc_dev(h->bcbox, 6ull * nc))
+      return DT_ENOMEM;
+    h->cap_bclouds = nc;
+  }
+  if (T > h->cap_tets) {
+    if (!realloc_dev(h->tets, T) || !realloc_dev(h->claim, 2 * T)) return DT_ENOMEM;
+    h->cap_tets = T;
+  }
+  if (T > h->cap_free) {
+    if (!realloc_dev(h->freelist, T) || !realloc_dev(h->pending, T)) return DT_ENOMEM;
+    h->cap_free = T;
+  }
+  if (!h->bstats && (!realloc_dev(h->bstats, kBatchStatSlots) || !realloc_dev(h->bnext, 1))) return DT_ENOMEM;
+  // workspaces and states for the largest grid of any block shape
+  int shapes[8];
+  int ns = batch_shapes(shapes, 8);
+  uint64_t states = 0;
+  size_t ws = 0;
+  const int sms = sm_count();
+  for (int i = 0; i < ns; ++i) {
+    uint64_t blocks = (uint64_t)std::max(1, batch_blocks_per_sm(shapes[i])) * sms;
+    states = std::max(states, blocks);
+    ws = std::max(ws, (size_t)blocks * shapes[i] * batch_ws_stride());
+  }
+  if (states > h->cap_bstates) {
+    if (!realloc_dev(h->bstates, states)) return DT_ENOMEM;
+    cudaMemsetAsync(h->bstates, 0, states * sizeof(DevState), h->stream);
+    h->cap_bstates = states;
+  }
+  if (ws > h->cap_bws) {
+    if (!realloc_dev(h->bws, ws)) return DT_ENOMEM;
+    h->cap_bws = ws;
+  }
+  return DT_OK;
+}
+
+Ctx batch_ctx(dt_handle* h) {
+  Ctx c = make_ctx(h);
+  c.coherent = 1;  // a block reads back the tetrahedra it writes
+  c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : 96u;
+  return c;
+}
+
+// One persistent launch over order[0 .. n) with block shape W; returns its device time (ms) or
+// a negative value when the launch failed.
+float batch_run(dt_handle* h, int W, float alpha, const uint32_t* order, uint32_t n, bool reset_all) {
+  cudaStream_t s = h->stream;
+  batch_reset(h->bclouds, reset_all ? nullptr : order, reset_all ? h->n_clouds : n, h->claim, h->bhint_f, h->bhint_c,
+              h->bdup, h->vflag, h->point_hint, s);
+  cudaMemsetAsync(h->bnext, 0, 4, s);
+  cudaMemsetAsync(h->bstats, 0, kBatchStatSlots * 8, s);
+  const unsigned blocks = (unsigned)std::max(1, batch_blocks_per_sm(W)) * (unsigned)sm_count();
+  cudaEventRecord(h->ev[3], s);
+  int rc = batch_launch(W, std::min<unsigned>(blocks, n), batch_ctx(h), h->bclouds, order, n, h->bnext, h->vflag,
+                        h->blist_a, h->blist_b, h->blist_big, h->bhint_f, h->bhint_c, h->bstates, h->bws,
+                        batch_ws_stride(), alpha, h->gamma, h->bstats, s);
+  cudaEventRecord(h->ev[4], s);
+  if (rc != DT_OK || cudaStreamSynchronize(s) != cudaSuccess) return -1.f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]);
+  return ms;
+}
+
+// Autotuner: block shape (warps per block) and round size (concurrent insertions per mesh
+// vertex) timed on a sample of the clouds spread over the size order; the fastest is kept for
+// batches with the same signature (cloud count and size range).
+int batch_tune(dt_handle* h, const std::vector<uint32_t>& by_size) {
+  const uint32_t nc = h->n_clouds;
+  uint64_t big = h->boff[by_size[0] + 1] - h->boff[by_size[0]];
+  uint64_t sig = ((uint64_t)nc << 40) ^ ((uint64_t)(64 - __builtin_clzll(h->boff[nc] | 1)) << 32) ^
+                 (uint64_t)(64 - __builtin_clzll(big | 1));
+  const char* fw = std::getenv("DT_BATCH_WARPS");
+  const char* fa = std::getenv("DT_BATCH_ALPHA");
+  if (fw && fa) {
+    h->batch_W = std::atoi(fw);
+    h->batch_alpha = (float)std::atof(fa);
+    h->batch_sig = sig;
+    return DT_OK;
+  }
+  if (h->batch_W && h->batch_sig == sig) return DT_OK;
+  // the sample: every k-th cloud of the size order, enough to fill the GPU a few times
+  const uint32_t want = std::min<uint32_t>(nc, std::max<uint32_t>(4u * (uint32_t)sm_count(), nc / 8));
+  const uint32_t step = std::max<uint32_t>(1, nc / std::max<uint32_t>(want, 1));
+  std::vector<uint32_t> sample;
+  for (uint32_t k = 0; k < nc && sample.size() < want; k += step) sample.push_back(by_size[k]);
+  if (cudaMemcpyAsync(h->bsample, sample.data(), sample.size() * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return DT_ECUDA;
+  int shapes[8];
+  int ns = batch_shapes(shapes, 8);
+  static const float kAlphas[] = {0.1f, 0.3f};
+  float best = -1.f;
+  auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < ns; ++i) {
+    if (fw && std::atoi(fw) != shapes[i]) continue;
+    for (float a : kAlphas) {
+      if (fa && std::fabs(std::atof(fa) - a) > 1e-6) continue;
+      float ms = batch_run(h, shapes[i], a, h->bsample, (uint32_t)sample.size(), false);
+      if (ms < 0.f) return DT_ECUDA;
+      if (best < 0.f || ms < best) {
+        best = ms;
+        h->batch_W = shapes[i];
+        h->batch_alpha = a;
+      }
+    }
+  }
+  h->batch_tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h->batch_sig = sig;
+  return h->batch_W ? DT_OK : DT_ELIMIT;
+}
+
+int batch_impl(dt_handle* h, const double* xyz, const uint64_t* off, uint32_t nc) {
+  cudaStream_t s = h->stream;
+  const uint64_t N = off[nc];
+  double f = h->cfg.tet_capacity_factor > 0 ? h->cfg.tet_capacity_factor : 8.0;
+  // slots per cloud: f per point plus room for the first tetrahedra and ghosts
+  std::vector<BatchCloud> cl(nc);
+  uint64_t T = 0;
+  for (uint32_t c = 0; c < nc; ++c) {
+    uint64_t n = off[c + 1] - off[c];
+    uint64_t cap = (uint64_t)(f * (double)n) + 64;
+    cl[c] = BatchCloud{};
+    cl[c].vb = (uint32_t)off[c];
+    cl[c].ve = (uint32_t)off[c + 1];
+    cl[c].tb = (uint32_t)T;
+    cl[c].tcap = (uint32_t)cap;
+    T += cap;
+  }
+  if (T > 0x3FFFFFFFull) return DT_ENOMEM;  // 4 t + facet must fit 32 bits
+  int rc = batch_reserve(h, N, nc, T);
+  if (rc != DT_OK) return rc;
+  h->n_clouds = nc;
+  h->boff.assign(off, off + nc + 1);
+  if (cudaMemcpyAsync(h->boff_dev, off, (nc + 1) * 8ull, cudaMemcpyHostToDevice, s) != cudaSuccess) return DT_ECUDA;
+  cudaEventRecord(h->ev[0], s);
+  if ((rc = order_batch(xyz, N, h->boff_dev, nc, h->cfg.seed, h->gamma, h->ows, h->bcid, h->bcbox, s)) != DT_OK)
+    return rc;
+  k_build_pts<<<grid_for(N, 256), 256, 0, s>>>(xyz, h->ows.perm, h->ows.dup, N, 0, h->pts, h->ptf, h->vflag,
+                                                h->point_hint);
+  ++g_kernel_launches;
+  cudaMemcpyAsync(h->bdup, h->vflag, N, cudaMemcpyDeviceToDevice, s);
+  cudaEventRecord(h->ev[1], s);
+  std::vector<double> box(6ull * nc);
+  if (cudaMemcpyAsync(box.data(), h->bcbox, 48ull * nc, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DT_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
+  h->cmax = 0.0;
+  const double cells = (double)(1u << batch_cb());
+  for (uint32_t c = 0; c < nc; ++c) {
+    for (int k = 0; k < 6; ++k) h->cmax = std::max(h->cmax, std::fabs(box[6ull * c + k]));
+    for (int k = 0; k < 3; ++k) {
+      double ext = box[6ull * c + 3 + k] - box[6ull * c + k];
+      cl[c].lo[k] = (float)box[6ull * c + k];
+      cl[c].sc[k] = ext > 0 ? (float)(cells / ext) : 0.f;
+    }
+  }
+  std::vector<uint32_t> by_size(nc);
+  for (uint32_t c = 0; c < nc; ++c) by_size[c] = c;
+  std::stable_sort(by_size.begin(), by_size.end(), [&](uint32_t a, uint32_t b) {
+    return off[a + 1] - off[a] > off[b + 1] - off[b];
+  });
+  cudaMemcpyAsync(h->bclouds, cl.data(), nc * sizeof(BatchCloud), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->border, by_size.data(), nc * 4ull, cudaMemcpyHostToDevice, s);
+  h->n_pts = N;
+  h->batch_mode = true;
+  if ((rc = batch_tune(h, by_size)) != DT_OK) return rc;
+  float ms = batch_run(h, h->batch_W, h->batch_alpha, h->border, nc, true);
+  if (ms < 0.f) return DT_ECUDA;
+  // results: per-cloud status and sizes, and the batch counters
+  h->bclouds_host.resize(nc);
+  unsigned long long st[kBatchStatSlots];
+  cudaMemcpyAsync(h->bclouds_host.data(), h->bclouds, nc * sizeof(BatchCloud), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(st, h->bstats, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
+  float ms_sort = 0.f;
+  cudaEventElapsedTime(&ms_sort, h->ev[0], h->ev[1]);
+  DevState agg{};
+  uint64_t degenerate = 0, used = 0;
+  for (const BatchCloud& b : h->bclouds_host) {
+    used += b.used;
+    if (b.status == kErrDegenerate) {
+      ++degenerate;
+    } else if (b.status != 0 && h->last_dev_error == 0) {
+      h->last_dev_error = b.status;
+      h->last_dev_info = b.info;
+    }
+  }
+  agg.n_inserted = st[0];
+  agg.n_conflicts = st[1];
+  agg.n_attempts = st[2];
+  agg.sum_cavity = st[3];
+  agg.sum_ball = st[4];
+  agg.sum_walk = st[5];
+  agg.n_big = st[7];
+  agg.n_exact = st[9];
+  agg.n_sos = st[10];
+  agg.bump = used;
+  std::memcpy(h->st_host, &agg, sizeof(agg));
+  h->stats.ms_sort = ms_sort;
+  h->stats.ms_insert = ms;
+  h->stats.n_rounds = st[8];
+  h->stats.n_passes = 0;
+  h->stats.n_clouds_degenerate = degenerate;
+  h->stats.batch_warps = (uint64_t)h->batch_W;
+  h->stats.batch_alpha = h->batch_alpha;
+  h->stats.ms_batch_tune = h->batch_tune_ms;
+  // DT_EDEGENERATE only when no cloud could be triangulated
+  if (h->last_dev_error) return map_dev_error(h->last_dev_error);
+  return degenerate == nc ? DT_EDEGENERATE : DT_OK;
+}
+
+// Finite tetrahedra of a batch, grouped by cloud (cloud-local ids).
+int batch_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets, uint64_t* cloud_offsets,
+                   int canonical) {
+  cudaStream_t s = h->stream;
+  const uint32_t nc = h->n_clouds;
+  unsigned long long *counts = nullptr, *ooff = nullptr;
+  if (cudaMalloc(&counts, nc * 8ull) != cudaSuccess) return DT_ENOMEM;
+  if (cudaMalloc(&ooff, (nc + 1) * 8ull) != cudaSuccess) {
+    cudaFree(counts);
+    return DT_ENOMEM;
+  }
+  cudaMemsetAsync(counts, 0, nc * 8ull, s);
+  batch_collect(h->bclouds, nc, h->tets, h->pts, h->boff_dev, 0, counts, nullptr, nullptr, canonical, s);
+  std::vector<unsigned long long> cnt(nc), oo(nc + 1, 0);
+  cudaMemcpyAsync(cnt.data(), counts, nc * 8ull, cudaMemcpyDeviceToHost, s);
+  int rc = cudaStreamSynchronize(s) == cudaSuccess ? DT_OK : DT_ECUDA;
+  for (uint32_t c = 0; c < nc; ++c) oo[c + 1] = oo[c] + cnt[c];
+  const uint64_t T = oo[nc];
+  *n_tets = T;
+  h->stats.n_tets = T;
+  if (cloud_offsets)
+    for (uint32_t c = 0; c <= nc; ++c) cloud_offsets[c] = oo[c];
+  if (rc == DT_OK && T > cap) rc = DT_ETOOSMALL;
+  uint32_t* tmp = nullptr;
+  if (rc == DT_OK && T > 0 && cudaMalloc(&tmp, T * 16) != cudaSuccess) rc = DT_ENOMEM;
+  if (rc == DT_OK && T > 0) {
+    cudaMemcpyAsync(ooff, oo.data(), (nc + 1) * 8ull, cudaMemcpyHostToDevice, s);
+    batch_collect(h->bclouds, nc, h->tets, h->pts, h->boff_dev, 1, counts, ooff, tmp, canonical, s);
+    if (canonical && !(h->cfg.flags & DT_FLAG_NO_CANONICAL_SORT) && T > 1) {
+      // lexicographic by (cloud, a, b, c, d): LSD passes on (c, d), then (a, b), then the cloud
+      uint64_t *khi = nullptr, *klo = nullptr, *kcl = nullptr, *ka = nullptr;
+      uint32_t *idx = nullptr, *ia = nullptr, *hist = nullptr;
+      bool ok = cudaMalloc(&khi, T * 8) == cudaSuccess && cudaMalloc(&klo, T * 8) == cudaSuccess &&
+                cudaMalloc(&kcl, T * 8) == cudaSuccess && cudaMalloc(&ka, T * 8) == cudaSuccess &&
+                cudaMalloc(&idx, T * 4) == cudaSuccess && cudaMalloc(&ia, T * 4) == cudaSuccess &&
+                cudaMalloc(&hist, radix_hist_entries(T) * 4) == cudaSuccess;
+      if (ok) {
+        int cbits = 8;
+        while (cbits < 32 && (1ull << cbits) < nc) cbits += 8;
+        batch_tet_keys(tmp, T, ooff, nc, khi, klo, kcl, idx, s);
+        bool alt = radix_sort_pairs(klo, idx, ka, ia, T, 64, hist, s);
+        uint32_t* order = alt ? ia : idx;
+        uint32_t* other = alt ? idx : ia;
+        k_gather_keys<<<grid_for(T, 256), 256, 0, s>>>(khi, order, T, ka);
+        ++g_kernel_launches;
+        bool alt2 = radix_sort_pairs(ka, order, klo, other, T, 64, hist, s);
+        uint32_t* order2 = alt2 ? other : order;
+        uint32_t* other2 = alt2 ? order : other;
+        k_gather_keys<<<grid_for(T, 256), 256, 0, s>>>(kcl, order2, T, ka);
+        ++g_kernel_launches;
+        bool alt3 = radix_sort_pairs_bits(ka, order2, klo, other2, T, 0, cbits, hist, s);
+        k_gather_tets<<<grid_for(T, 256), 256, 0, s>>>((const uint4*)tmp, alt3 ? other2 : order2, T,
+                                                       (uint4*)tets_dev);
+        ++g_kernel_launches;
+      } else {
+        rc = DT_ENOMEM;
+      }
+      cudaFree(khi);
+      cudaFree(klo);
+      cudaFree(kcl);
+      cudaFree(ka);
+      cudaFree(idx);
+      cudaFree(ia);
+      cudaFree(hist);
+    } else {
+      cudaMemcpyAsync(tets_dev, tmp, T * 16, cudaMemcpyDeviceToDevice, s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = DT_ECUDA;
+  }
+  cudaFree(tmp);
+  cudaFree(counts);
+  cudaFree(ooff);
+  return rc;
+}
+
 void fill_stats(dt_handle* h, dt_stats* o) {
   *o = h->stats;
   o->n_launches = g_kernel_launches - h->launches0;
@@ -1304,9 +1468,9 @@ void fill_stats(dt_handle* h, dt_stats* o) {
   o->sum_walk = d.sum_walk;
   o->n_exact = d.n_exact;
   o->n_sos = d.n_sos;
-  o->reserved[0] = d.n_walk_limit;
-  o->reserved[1] = d.free_avail;
-  o->reserved[2] = d.max_walk;
+  o->n_walk_limit = d.n_walk_limit;
+  o->free_slots = d.free_avail;
+  o->max_walk = d.max_walk;
 }
 
 }  // namespace
@@ -1355,6 +1519,13 @@ int dt_clear(dt_handle* h) {
   unsigned long long s = h->has_mesh ? h->st_host->stamp : 0;
   h->next_stamp = std::max(h->next_stamp, s + 1);
   h->has_mesh = false;
+  if (h->batch_mode) {
+    // a batch restarts its claim stamps in every cloud: clear the words before anything else
+    if (h->claim && cudaMemsetAsync(h->claim, 0, 2 * h->cap_tets * sizeof(unsigned long long), h->stream) != cudaSuccess)
+      return DT_ECUDA;
+    h->batch_mode = false;
+    h->n_clouds = 0;
+  }
   h->n_pts = 0;
   h->last_n = 0;
   h->cmax = 0.0;
@@ -1367,11 +1538,13 @@ int dt_clear(dt_handle* h) {
 
 int dt_insert(dt_handle* h, const double* xyz_dev, uint64_t n) {
   if (!h || (n > 0 && !xyz_dev)) return DT_EINVAL;
+  if (h->batch_mode) return DT_ESTATE;
   return insert_impl(h, xyz_dev, n);
 }
 
 int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n) {
   if (!h || (n > 0 && !xyz_host)) return DT_EINVAL;
+  if (h->batch_mode) return DT_ESTATE;
   double* d = nullptr;
   if (n && cudaMalloc(&d, n * 24) != cudaSuccess) return DT_ENOMEM;
   if (n && cudaMemcpyAsync(d, xyz_host, n * 24, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
@@ -1385,18 +1558,23 @@ int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n) {
 }
 
 int dt_batch(dt_handle* h, const double* xyz_dev, const uint64_t* offsets_host, uint32_t n_clouds) {
-  (void)xyz_dev;
-  (void)offsets_host;
-  (void)n_clouds;
-  if (!h) return DT_EINVAL;
-  return DT_ESTATE;
+  if (!h || !offsets_host || n_clouds == 0 || offsets_host[0] != 0) return DT_EINVAL;
+  for (uint32_t c = 0; c < n_clouds; ++c)
+    if (offsets_host[c + 1] < offsets_host[c]) return DT_EINVAL;
+  const uint64_t N = offsets_host[n_clouds];
+  if (N == 0 || !xyz_dev || N >= 0xFFFFFFF0ull) return DT_EINVAL;
+  int rc = dt_clear(h);
+  if (rc != DT_OK) return rc;
+  rc = batch_impl(h, xyz_dev, offsets_host, n_clouds);
+  if (rc != DT_OK && rc != DT_EDEGENERATE && h->last_dev_error == 0) h->last_dev_error = 0;
+  return rc;
 }
 
 int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets, uint64_t* cloud_offsets,
                 int canonical) {
-  (void)cloud_offsets;
   if (!h || !n_tets || (cap > 0 && !tets_dev)) return DT_EINVAL;
   *n_tets = 0;
+  if (h->batch_mode) return batch_get_tets(h, tets_dev, cap, n_tets, cloud_offsets, canonical);
   if (!h->has_mesh) return DT_OK;
   cudaStream_t s = h->stream;
   int rc = sync_state(h);
@@ -1530,6 +1708,22 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->hugemem);
   cudaFree(h->ctamem);
   cudaFree(h->bbox_dev);
+  cudaFree(h->boff_dev);
+  cudaFree(h->bclouds);
+  cudaFree(h->border);
+  cudaFree(h->bsample);
+  cudaFree(h->bcid);
+  cudaFree(h->bdup);
+  cudaFree(h->blist_a);
+  cudaFree(h->blist_b);
+  cudaFree(h->blist_big);
+  cudaFree(h->bhint_f);
+  cudaFree(h->bhint_c);
+  cudaFree(h->bcbox);
+  cudaFree(h->bstates);
+  cudaFree(h->bws);
+  cudaFree(h->bstats);
+  cudaFree(h->bnext);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->prof_events) cudaEventDestroy(e);

@@ -164,7 +164,7 @@ __device__ __forceinline__ int orient_replace(const Ctx& c, const uint4& v, int 
 
 // Returns kCandLocated (*t_out in conflict with p), kCandWalkLimit (*t_out = where it stopped)
 // or kCandDup (p equals a vertex of the tetrahedron reached).
-__device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32_t start, uint32_t salt, uint32_t anchor,
+static __device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32_t start, uint32_t salt, uint32_t anchor,
                           uint32_t max_steps, uint32_t* t_out, uint32_t* steps_out) {
   uint32_t t = start;
   Tet T;
@@ -254,7 +254,7 @@ __device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32_t star
 // Perturbed insphere of a finite tetrahedron and p: negative = p inside (FP32 stage first).
 // FP64 (then exact, then perturbed) insphere, out of line: the FP32 stage settles nearly every
 // test, and keeping this path out of the callers keeps their registers for the common case.
-__device__ __noinline__ bool inside_finite_fp64(const Ctx& c, uint4 v, uint32_t p) {
+static __device__ __noinline__ bool inside_finite_fp64(const Ctx& c, uint4 v, uint32_t p) {
   Pt a = load_pt(c.pts, v.x), b = load_pt(c.pts, v.y), d = load_pt(c.pts, v.z), e = load_pt(c.pts, v.w);
   return insphere_sos(a, b, d, e, load_pt(c.pts, p), c.st) < 0;
 }
@@ -269,7 +269,7 @@ __device__ __forceinline__ bool inside_finite(const Ctx& c, const uint4& v, uint
 // Membership of tetrahedron u in the cavity of p: perturbed insphere for a finite tetrahedron;
 // for a ghost, p strictly beyond its hull facet, or on the facet's plane and inside the
 // perturbed sphere of the finite neighbour across it (Section 2.6).
-__device__ bool in_conflict(const Ctx& c, uint32_t u, uint32_t p, const PtF& FP) {
+static __device__ bool in_conflict(const Ctx& c, uint32_t u, uint32_t p, const PtF& FP) {
   Tet U = tet_at(c, u);
   if (!tet_sane(c, U) || tet_dead(U.v)) {
     raise_error(c.st, kErrInternal, 0xB000u);
@@ -332,7 +332,7 @@ __device__ __forceinline__ bool ws_insert(const CavWS& w, uint32_t key, uint8_t 
 // ------------------------------------------------------------------ cavity (warp)
 // Returns kCandLocated (C in w.clist[0..nc), boundary facets in w.blist[0..nb)), kCandLost
 // (saw a higher-priority claim) or kCandBig (exceeds this workspace).
-__device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uint32_t p, const PtF& FP,
+static __device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uint32_t p, const PtF& FP,
                            unsigned long long prio, int* nc_out, int* nb_out) {
   const int lane = threadIdx.x & 31;
   for (uint32_t i = lane; i <= w.hmask; i += 32) w.hkey[i] = kNone;
@@ -452,7 +452,7 @@ __device__ __forceinline__ uint32_t edge_slot(const InsWS& w, unsigned long long
 // ------------------------------------------------------------------ ball (warp)
 // Verifies the claims of a located point and, if it won, replaces its cavity by the ball.
 // Returns kCandInserted or kCandLost. alloc: allocator snapshot of this round.
-__device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned long long prio,
+static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned long long prio,
                            const uint32_t* clist, int nc, const uint32_t* blist, int nb,
                            bool use_table, unsigned long long fa, unsigned long long bump,
                            unsigned long long cap) {
@@ -611,6 +611,196 @@ __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsigned lo
     __threadfence();  // the warp that closes the round reads these entries
   }
   return kCandInserted;
+}
+
+// ------------------------------------------------------------------ global-memory workspaces
+struct BigWS {
+  CavWS cav;
+  InsWS ins;
+};
+
+// Carves the workspaces of one candidate out of a byte range (global memory).
+__host__ __device__ inline size_t carve(char* base, uint32_t hashn, uint32_t cn, uint32_t fn, uint32_t edgen,
+                                        BigWS* w) {
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    char* r = base ? base + off : nullptr;
+    off += (n + 15) & ~size_t(15);
+    return r;
+  };
+  BigWS x{};
+  x.ins.ekey = (unsigned long long*)take((size_t)edgen * 8);
+  x.ins.nv = (uint4*)take((size_t)fn * 16);
+  x.ins.nn = (uint4*)take((size_t)fn * 16);
+  x.cav.hkey = (uint32_t*)take((size_t)hashn * 4);
+  x.cav.clist = (uint32_t*)take((size_t)cn * 4);
+  x.cav.blist = (uint32_t*)take((size_t)fn * 4);
+  x.ins.eval = (uint32_t*)take((size_t)edgen * 4);
+  x.ins.hslot = (uint32_t*)take((size_t)fn * 3 * 4);
+  x.ins.hold = (uint32_t*)take((size_t)fn * 3 * 4);
+  x.ins.outh = (uint32_t*)take((size_t)fn * 4);
+  x.ins.slot = (uint32_t*)take((size_t)fn * 4);
+  x.ins.vkey = (uint32_t*)take(32 * 4);
+  x.ins.tab = (uint16_t*)take(32 * 32 * 2);
+  x.cav.hval = (uint8_t*)take(hashn);
+  x.ins.ipos = (uint8_t*)take(fn);
+  x.cav.hmask = hashn - 1;
+  x.cav.cmax = cn;
+  x.cav.bmax = fn;
+  x.ins.emask = edgen - 1;
+  if (w) *w = x;
+  return off;
+}
+
+// ------------------------------------------------------------------ rounds and init
+// Closes a round (run by the last block of the insert kernel): the allocator consumed the top
+// of the free list, then the bump pointer; slots freed during the round join the free list;
+// the claim stamp advances.
+static __device__ void finish_round_block(const Ctx& c) {
+  DevState* st = c.st;
+  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
+  unsigned long long np = __ldcg(&st->pending);
+  __syncthreads();
+  unsigned long long consumed = used < fa ? used : fa;
+  unsigned long long nfa = fa - consumed;
+  if (nfa + np > st->free_capacity) {
+    if (threadIdx.x == 0) raise_error(st, kErrFreeList, 0);
+    np = st->free_capacity - nfa;
+  }
+  for (unsigned long long i = threadIdx.x; i < np; i += blockDim.x) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->bump += used - consumed;
+    st->free_avail = nfa + np;
+    st->alloc_cursor = 0;
+    st->pending = 0;
+    st->stamp += 1;
+    st->blocks_done = 0;
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Closes a round run by a single warp (the serial path, and the last warp of the insert kernel).
+static __device__ void finish_round_warp(const Ctx& c) {
+  const int lane = threadIdx.x & 31;
+  DevState* st = c.st;
+  unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
+  unsigned long long np = __ldcg(&st->pending);
+  __syncwarp();
+  unsigned long long consumed = used < fa ? used : fa;
+  unsigned long long nfa = fa - consumed;
+  if (nfa + np > st->free_capacity) {
+    if (lane == 0) raise_error(st, kErrFreeList, 0);
+    np = st->free_capacity - nfa;
+  }
+  for (unsigned long long i = lane; i < np; i += 32) c.freelist[nfa + i] = __ldcg(&c.pending[i]);
+  __syncwarp();
+  if (lane == 0) {
+    st->bump += used - consumed;
+    st->free_avail = nfa + np;
+    st->alloc_cursor = 0;
+    st->pending = 0;
+    st->stamp += 1;
+    st->blocks_done = 0;
+  }
+  __threadfence();
+  __syncwarp();
+}
+
+// Init (Section 2.1): the first four non-coplanar vertices of the insertion order form a
+// positive tetrahedron; four ghost tetrahedra close it (Section 2.6). The five records go to
+// slots tbase .. tbase + 4. Returns false (and raises kErrDegenerate) when [vbegin, vend) holds
+// fewer than four non-coplanar vertices. One thread.
+static __device__ bool init_mesh(const Ctx& c, uint32_t vbegin, uint32_t vend, uint8_t* vflag, uint32_t tbase) {
+  uint32_t s = vbegin;
+  while (s < vend && vflag[s]) ++s;
+  uint32_t i0 = s++;
+  while (s < vend && vflag[s]) ++s;
+  uint32_t i1 = s++;
+  if (i1 >= vend) {
+    raise_error(c.st, kErrDegenerate, 0);
+    return false;
+  }
+  Pt A = c.pts[i0], B = c.pts[i1];
+  while (s < vend && (vflag[s] || collinear_exact(A, B, c.pts[s], c.st))) ++s;
+  uint32_t i2 = s++;
+  if (i2 >= vend) {
+    raise_error(c.st, kErrDegenerate, 1);
+    return false;
+  }
+  Pt C = c.pts[i2];
+  while (s < vend && (vflag[s] || orient3d(A, B, C, c.pts[s], c.st) == 0)) ++s;
+  uint32_t i3 = s;
+  if (i3 >= vend) {
+    raise_error(c.st, kErrDegenerate, 2);
+    return false;
+  }
+  uint32_t v[4] = {i0, i1, i2, i3};
+  if (orient3d(A, B, C, c.pts[i3], c.st) < 0) {
+    v[2] = i3;
+    v[3] = i2;
+  }
+  uint32_t tv[5][4];
+  for (int k = 0; k < 4; ++k) tv[0][k] = v[k];
+  for (int i = 0; i < 4; ++i) {
+    for (int k = 0; k < 4; ++k) tv[1 + i][k] = v[k];
+    tv[1 + i][i] = kGhost;
+    int a = (i == 0) ? 1 : 0, b = (i <= 1) ? 2 : 1;
+    uint32_t x = tv[1 + i][a];
+    tv[1 + i][a] = tv[1 + i][b];
+    tv[1 + i][b] = x;
+  }
+  uint32_t nn[5][4];
+  for (int t = 0; t < 5; ++t)
+    for (int f = 0; f < 4; ++f) {
+      nn[t][f] = kNone;
+      for (int u = 0; u < 5 && nn[t][f] == kNone; ++u) {
+        if (u == t) continue;
+        for (int g = 0; g < 4; ++g) {
+          // facet f of t equals facet g of u when the other three vertices coincide as sets
+          int match = 0;
+          for (int a = 0; a < 4; ++a) {
+            if (a == f) continue;
+            for (int b = 0; b < 4; ++b)
+              if (b != g && tv[t][a] == tv[u][b]) {
+                ++match;
+                break;
+              }
+          }
+          if (match == 3) {
+            nn[t][f] = 4u * (tbase + u) + g;
+            break;
+          }
+        }
+      }
+    }
+  for (int t = 0; t < 5; ++t) {
+    c.tets[tbase + t].v = make_uint4(tv[t][0], tv[t][1], tv[t][2], tv[t][3]);
+    c.tets[tbase + t].n = make_uint4(nn[t][0], nn[t][1], nn[t][2], nn[t][3]);
+  }
+  vflag[i0] = vflag[i1] = vflag[i2] = vflag[i3] = 2;
+  c.st->bump = tbase + 5;
+  c.st->anchor = tbase;
+  c.st->n_inserted += 4;
+  return true;
+}
+
+// Canonical form of a positively oriented tetrahedron (vertex ids r[0..3]): the even permutation
+// that brings the smallest id first, then the cyclic turn of the other three that starts at
+// their smallest. Orientation is preserved.
+__device__ __forceinline__ void canonical_rotation(uint32_t r[4]) {
+  int k = 0;
+  for (int i = 1; i < 4; ++i)
+    if (r[i] < r[k]) k = i;
+  uint32_t a[4];
+  if (k == 0) { a[0] = r[0]; a[1] = r[1]; a[2] = r[2]; a[3] = r[3]; }
+  else if (k == 1) { a[0] = r[1]; a[1] = r[0]; a[2] = r[3]; a[3] = r[2]; }
+  else if (k == 2) { a[0] = r[2]; a[1] = r[0]; a[2] = r[1]; a[3] = r[3]; }
+  else { a[0] = r[3]; a[1] = r[0]; a[2] = r[2]; a[3] = r[1]; }
+  if (a[2] < a[1] && a[2] < a[3]) { uint32_t x = a[1]; a[1] = a[2]; a[2] = a[3]; a[3] = x; }
+  else if (a[3] < a[1] && a[3] < a[2]) { uint32_t x = a[3]; a[3] = a[2]; a[2] = a[1]; a[1] = x; }
+  for (int i = 0; i < 4; ++i) r[i] = a[i];
 }
 
 }  // namespace dtg

@@ -12,6 +12,63 @@ namespace dtg {
 // Kernels launched by this library (all handles), for the launch counts the bench reports.
 extern unsigned long long g_kernel_launches;
 
+// ---------------------------------------------------------------- waves (both engines)
+// A BRIO round of m points joins a mesh of about n0 vertices in waves: each wave takes
+// ceil(gamma * N) more points of the round (N = mesh size before the wave), so the number of
+// concurrent insertions can follow the mesh as it grows. Points go to waves by their hash rank
+// inside the round (a uniformly random subset per wave). At most kMaxWaves waves per round.
+constexpr int kMaxWaves = 255;
+
+// End (exclusive, in ranks) of wave k of a round of m points joining n0 vertices.
+__host__ __device__ inline uint64_t wave_end(uint64_t m, uint64_t n0, double gamma, int k) {
+  double N = (double)(n0 < 4 ? 4 : n0);
+  uint64_t acc = 0;
+  for (int i = 0; i <= k && acc < m; ++i) {
+    double w = ceil(gamma * N);
+    uint64_t wi = w < 1.0 ? 1 : (uint64_t)w;
+    acc = (i == kMaxWaves - 1 || acc + wi > m) ? m : acc + wi;
+    N += (double)wi;
+  }
+  return acc;
+}
+
+// Wave of the point of rank r (0 <= r < m) inside its round.
+__host__ __device__ inline int wave_of(uint64_t r, uint64_t m, uint64_t n0, double gamma) {
+  double N = (double)(n0 < 4 ? 4 : n0);
+  uint64_t acc = 0;
+  for (int i = 0; i < kMaxWaves; ++i) {
+    double w = ceil(gamma * N);
+    uint64_t wi = w < 1.0 ? 1 : (uint64_t)w;
+    acc = (i == kMaxWaves - 1 || acc + wi > m) ? m : acc + wi;
+    if (r < acc) return i;
+    N += (double)wi;
+  }
+  return kMaxWaves - 1;
+}
+
+// First input rank of BRIO round r (cumulative sizes of Table 2: 2048, x 7 per round).
+__host__ __device__ inline uint64_t brio_round_begin(int r) {
+  uint64_t e = 0, s = 2048;
+  for (int i = 0; i < r; ++i) {
+    e = s;
+    s *= 7;
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------- batch of clouds
+// One cloud of a batch. Its vertices are the sorted positions [vb, ve) (the same rows as its
+// input), its tetrahedra the slots [tb, tb + tcap).
+struct BatchCloud {
+  uint32_t vb, ve;
+  uint32_t tb, tcap;
+  float lo[3], sc[3];  // 8 x 8 x 8 hint grid over the cloud's box
+  uint32_t used;       // out: slots used (from tb)
+  uint32_t status;     // out: 0 = triangulated, else the device error code (kErr*)
+  uint32_t info;       // out: the error's detail
+  uint32_t inserted;   // out: vertices in the triangulation
+};
+
 // ---------------------------------------------------------------- order.cu (S1-S4)
 // Device workspace for ordering up to `cap` points.
 struct OrderWS {
@@ -39,6 +96,15 @@ void order_ws_free(OrderWS& ws);
 // and ws.perm (insertion order). Returns DT_OK, DT_EINVAL (bad coordinates) or DT_ECUDA.
 int order_points(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cudaStream_t s);
 
+// S1..S4 for a batch of n_clouds clouds back to back (cloud c = input rows offsets_dev[c] ..
+// offsets_dev[c + 1], device array): each cloud gets its own box, Moore keys, duplicates and
+// BRIO ranks (ws.keys, ws.dup, ws.rounds, ws.rank by input index), and ws.perm orders the points
+// by (cloud, round, wave, key, index), so every cloud keeps its input rows' positions and every
+// wave (wave_of with gamma, n0 = the round's first rank) is a contiguous range. cid [n] and
+// cbox [6 n_clouds] (device) receive the cloud of every input index and every cloud's box.
+int order_batch(const double* xyz, uint64_t n, const uint64_t* offsets_dev, uint32_t n_clouds, uint64_t seed,
+                double gamma, OrderWS& ws, uint32_t* cid, double* cbox, cudaStream_t s);
+
 // Stable LSD radix sort of (key, value) pairs on bits [0, bits) of the keys. Ping-pongs between
 // (k, v) and (ka, va); returns true when the sorted result ended in (ka, va).
 bool radix_sort_pairs(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int bits,
@@ -56,4 +122,30 @@ uint64_t brio_round_end(int r);
 void transformed_keys(const Pt* pts, const uint32_t* ids, uint64_t m, const double* bbox,
                       uint64_t seed, uint64_t* keys_out, uint32_t* vals_out, cudaStream_t s);
 
+// ---------------------------------------------------------------- batch.cu (dt_batch)
+struct Ctx;
+size_t batch_ws_stride();       // bytes of one warp's workspace
+uint32_t batch_hint_fine();     // fine hint cells per cloud
+uint32_t batch_hint_coarse();   // coarse hint cells per cloud
+int batch_cb();                 // bits per axis of a cloud's fine hint grid
+int batch_shapes(int* warps, int max_n);  // block shapes (warps) the batch kernel is built for
+int batch_blocks_per_sm(int W);           // resident blocks per SM with W warps
+constexpr int kBatchStatSlots = 11;      // accumulators batch_launch adds into
+// One persistent launch over the clouds order[0 .. n_clouds) (see batch.cu); *next must be 0.
+int batch_launch(int W, unsigned blocks, const Ctx& c, BatchCloud* clouds, const uint32_t* order, uint32_t n_clouds,
+                 unsigned int* next, uint8_t* vflag, uint32_t* list_a, uint32_t* list_b, uint32_t* list_big,
+                 uint32_t* hint_fine, uint32_t* hint_coarse, DevState* states, char* wsmem, size_t wsstride,
+                 float alpha, double gamma, unsigned long long* stats, cudaStream_t s);
+// Resets the clouds list[0 .. n_list) (all clouds when list is null) for a new launch.
+void batch_reset(const BatchCloud* clouds, const uint32_t* list, uint32_t n_list, unsigned long long* claim,
+                 uint32_t* hint_fine, uint32_t* hint_coarse, const uint8_t* dup_sorted, uint8_t* vflag,
+                 uint32_t* point_hint, cudaStream_t s);
+// Finite tetrahedra per cloud with cloud-local ids: pass 0 counts into counts[c], pass 1
+// writes cloud c's from out_off[c].
+void batch_collect(const BatchCloud* clouds, uint32_t n_clouds, const Tet* tets, const Pt* pts, const uint64_t* in_off,
+                   int pass, unsigned long long* counts, const unsigned long long* out_off, uint32_t* out,
+                   int canonical, cudaStream_t s);
+// Sort keys of collected tetrahedra: (a, b), (c, d) and the cloud.
+void batch_tet_keys(const uint32_t* tets, uint64_t T, const unsigned long long* out_off, uint32_t n_clouds,
+                    uint64_t* khi, uint64_t* klo, uint64_t* kcl, uint32_t* idx, cudaStream_t s);
 }  // namespace dtg

@@ -261,6 +261,153 @@ __global__ void k_round_keys(const uint32_t* svals, uint64_t n, const uint8_t* r
     keys[s] = rounds[svals[s]];
 }
 
+// ------------------------------------------------------------------ batches of clouds
+// Cloud of every input index (cloud c holds input rows offsets[c] .. offsets[c + 1]).
+__global__ void k_batch_cid(const uint64_t* __restrict__ offsets, uint32_t n_clouds, uint32_t* cid) {
+  for (uint32_t c = blockIdx.x; c < n_clouds; c += gridDim.x)
+    for (uint64_t i = offsets[c] + threadIdx.x; i < offsets[c + 1]; i += blockDim.x) cid[i] = c;
+}
+
+// Bounding box of every cloud (one block per cloud), and the non-finite coordinate check.
+__global__ void k_batch_bbox(const double* __restrict__ xyz, const uint64_t* __restrict__ offsets,
+                             uint32_t n_clouds, double* bbox, unsigned int* bad) {
+  __shared__ double s[6][kBoxThreads];
+  for (uint32_t c = blockIdx.x; c < n_clouds; c += gridDim.x) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool b = false;
+    for (uint64_t i = offsets[c] + threadIdx.x; i < offsets[c + 1]; i += blockDim.x)
+      for (int k = 0; k < 3; ++k) {
+        double x = xyz[3 * i + k];
+        if (!(fabs(x) <= 1e30)) b = true;
+        lo[k] = fmin(lo[k], x);
+        hi[k] = fmax(hi[k], x);
+      }
+    if (b) atomicExch(bad, 1u);
+    for (int k = 0; k < 3; ++k) {
+      s[k][threadIdx.x] = lo[k];
+      s[3 + k][threadIdx.x] = hi[k];
+    }
+    __syncthreads();
+    for (int w = kBoxThreads / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w)
+        for (int k = 0; k < 3; ++k) {
+          s[k][threadIdx.x] = fmin(s[k][threadIdx.x], s[k][threadIdx.x + w]);
+          s[3 + k][threadIdx.x] = fmax(s[3 + k][threadIdx.x], s[3 + k][threadIdx.x + w]);
+        }
+      __syncthreads();
+    }
+    if (threadIdx.x < 6) bbox[6 * (uint64_t)c + threadIdx.x] = s[threadIdx.x][0];
+    __syncthreads();
+  }
+}
+
+// Moore key of every point on its own cloud's 2^21 grid (the same key dt_insert would give the
+// cloud on its own).
+__global__ void k_batch_moore(const double* __restrict__ xyz, uint64_t n, const uint32_t* __restrict__ cid,
+                              const double* __restrict__ bbox, uint64_t* keys, uint64_t* skeys, uint32_t* svals) {
+  __shared__ uint16_t step[24 * 8];
+  __shared__ uint16_t top[8];
+  for (int i = threadIdx.x; i < 24 * 8; i += blockDim.x) step[i] = kMoore.step[i];
+  if (threadIdx.x < 8) top[threadIdx.x] = kMoore.top[threadIdx.x];
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const double* B = bbox + 6 * (uint64_t)cid[i];
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+      double ext = B[3 + k] - B[k];
+      q[k] = quantise(xyz[3 * i + k], B[k], ext > 0.0 ? kCells / ext : 0.0);
+    }
+    uint64_t key = moore_of_cell(q[0], q[1], q[2], step, top);
+    keys[i] = key;
+    skeys[i] = key;
+    svals[i] = (uint32_t)i;
+  }
+}
+
+__global__ void k_batch_gather_cid(const uint32_t* __restrict__ svals, uint64_t n, const uint32_t* __restrict__ cid,
+                                   uint64_t* keys) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+       s += (uint64_t)gridDim.x * blockDim.x)
+    keys[s] = cid[svals[s]];
+}
+
+// Exact duplicates inside a cloud: they share the cloud and the key, so they sit in one run of
+// the (cloud, key) order, input indices ascending.
+__global__ void k_batch_dedup(const uint32_t* __restrict__ svals, uint64_t n, const uint64_t* __restrict__ keys,
+                              const uint32_t* __restrict__ cid, const double* __restrict__ xyz, uint8_t* dup) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = svals[s];
+    if (s > 0) {
+      uint32_t j = svals[s - 1];
+      if (keys[j] == keys[i] && cid[j] == cid[i]) continue;
+    }
+    uint64_t e = s + 1;
+    while (e < n && keys[svals[e]] == keys[i] && cid[svals[e]] == cid[i]) ++e;
+    for (uint64_t a = s + 1; a < e; ++a) {
+      uint32_t ia = svals[a];
+      for (uint64_t b = s; b < a; ++b) {
+        uint32_t ib = svals[b];
+        if (xyz[3 * (uint64_t)ia] == xyz[3 * (uint64_t)ib] &&
+            xyz[3 * (uint64_t)ia + 1] == xyz[3 * (uint64_t)ib + 1] &&
+            xyz[3 * (uint64_t)ia + 2] == xyz[3 * (uint64_t)ib + 2]) {
+          dup[ia] = 1;
+          break;
+        }
+      }
+    }
+  }
+}
+
+// BRIO keys inside each cloud: (cloud, top 32 bits of the hash of the cloud-local index).
+__global__ void k_batch_hash(uint64_t n, const uint32_t* __restrict__ cid, const uint64_t* __restrict__ offsets,
+                             uint64_t seed, uint64_t* keys, uint32_t* vals) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t c = cid[i];
+    uint64_t local = i - offsets[c];
+    keys[i] = ((uint64_t)c << 32) | (mix64((seed ^ local) + 0x9E3779B97F4A7C15ull) >> 32);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+// BRIO round of every point from its hash rank inside its cloud (Table 2 sizes).
+__global__ void k_batch_assign(const uint32_t* __restrict__ sorted_idx, uint64_t n, const uint32_t* __restrict__ cid,
+                               const uint64_t* __restrict__ offsets, uint8_t* rounds, uint32_t* rank) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = sorted_idx[s];
+    uint64_t r = s - offsets[cid[i]];
+    uint64_t end = 2048;
+    uint8_t k = 0;
+    while (r >= end) {
+      end *= 7;
+      ++k;
+    }
+    rounds[i] = k;
+    rank[i] = (uint32_t)r;
+  }
+}
+
+// (cloud, round, wave) of every point in the (cloud, key) order. A round joins a mesh of about
+// as many vertices as the rounds before it hold.
+__global__ void k_batch_round_keys(const uint32_t* __restrict__ svals, uint64_t n, const uint32_t* __restrict__ cid,
+                                   const uint64_t* __restrict__ offsets, const uint8_t* __restrict__ rounds,
+                                   const uint32_t* __restrict__ rank, double gamma, uint64_t* keys) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = svals[s];
+    uint32_t c = cid[i];
+    int r = rounds[i];
+    uint64_t nc = offsets[c + 1] - offsets[c];
+    uint64_t b = brio_round_begin(r), e = brio_round_begin(r + 1);
+    uint64_t m = (e < nc ? e : nc) - b;
+    int w = wave_of(rank[i] - b, m, b, gamma);
+    keys[s] = ((uint64_t)c << 16) | ((uint64_t)r << 8) | (uint64_t)w;
+  }
+}
+
 // ------------------------------------------------------------------ radix sort
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
@@ -512,6 +659,51 @@ int order_points(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cuda
   if (n == 0) return DT_OK;
   if (order_ws_reserve(ws, n) != cudaSuccess) return DT_ENOMEM;
   return order_points_ws(xyz, n, seed, ws, s);
+}
+
+int order_batch(const double* xyz, uint64_t n, const uint64_t* offsets_dev, uint32_t n_clouds, uint64_t seed,
+                double gamma, OrderWS& ws, uint32_t* cid, double* cbox, cudaStream_t s) {
+  if (n == 0) return DT_OK;
+  int cbits = 8;
+  while (cbits < 32 && (1ull << cbits) < n_clouds) cbits += 8;
+  cudaMemsetAsync(ws.bad, 0, 4, s);
+  cudaMemsetAsync(ws.dup, 0, n, s);
+  unsigned gc = (unsigned)std::min<uint32_t>(n_clouds, 152u * 16);
+  k_batch_cid<<<gc, 256, 0, s>>>(offsets_dev, n_clouds, cid);
+  k_batch_bbox<<<gc, kBoxThreads, 0, s>>>(xyz, offsets_dev, n_clouds, cbox, ws.bad);
+  unsigned g = grid_for(n, 256);
+  k_batch_moore<<<g, 256, 0, s>>>(xyz, n, cid, cbox, ws.keys, ws.k0, ws.v0);
+  g_kernel_launches += 3;
+  // (cloud, key, index) order: Moore keys, then a stable sort by cloud
+  bool alt = radix_sort_pairs(ws.k0, ws.v0, ws.k1, ws.v1, n, 64, ws.hist, s);
+  uint32_t* sv = alt ? ws.v1 : ws.v0;
+  uint32_t* ov = alt ? ws.v0 : ws.v1;
+  uint64_t* sk = alt ? ws.k1 : ws.k0;
+  uint64_t* ok = alt ? ws.k0 : ws.k1;
+  k_batch_gather_cid<<<g, 256, 0, s>>>(sv, n, cid, sk);
+  ++g_kernel_launches;
+  bool alt2 = radix_sort_pairs_bits(sk, sv, ok, ov, n, 0, cbits, ws.hist, s);
+  uint32_t* kv = alt2 ? ov : sv;
+  k_batch_dedup<<<g, 256, 0, s>>>(kv, n, ws.keys, cid, xyz, ws.dup);
+  ++g_kernel_launches;
+  cudaMemcpyAsync(ws.perm, kv, n * 4, cudaMemcpyDeviceToDevice, s);
+  // BRIO ranks inside each cloud
+  k_batch_hash<<<g, 256, 0, s>>>(n, cid, offsets_dev, seed, ws.k0, ws.v0);
+  ++g_kernel_launches;
+  bool alt3 = radix_sort_pairs_bits(ws.k0, ws.v0, ws.k1, ws.v1, n, 0, 32 + cbits, ws.hist, s);
+  k_batch_assign<<<g, 256, 0, s>>>(alt3 ? ws.v1 : ws.v0, n, cid, offsets_dev, ws.rounds, ws.rank);
+  ++g_kernel_launches;
+  // stable sort of the (cloud, key) order by (cloud, round, wave)
+  k_batch_round_keys<<<g, 256, 0, s>>>(ws.perm, n, cid, offsets_dev, ws.rounds, ws.rank, gamma, ws.k0);
+  ++g_kernel_launches;
+  cudaMemcpyAsync(ws.v0, ws.perm, n * 4, cudaMemcpyDeviceToDevice, s);
+  bool alt4 = radix_sort_pairs_bits(ws.k0, ws.v0, ws.k1, ws.v1, n, 0, cbits + 16, ws.hist, s);
+  cudaMemcpyAsync(ws.perm, alt4 ? ws.v1 : ws.v0, n * 4, cudaMemcpyDeviceToDevice, s);
+  unsigned int bad = 0;
+  cudaMemcpyAsync(&bad, ws.bad, 4, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
+  if (bad) return DT_EINVAL;
+  return DT_OK;
 }
 
 void transformed_keys(const Pt* pts, const uint32_t* ids, uint64_t m, const double* bbox,

@@ -179,7 +179,7 @@ __device__ __forceinline__ int ex_minor(const Ex2& a, const Ex2& b, const Ex2& c
 }
 
 // out = det[r0; r1; r2] for rows of exact differences, compressed; at most 193 components.
-__device__ __noinline__ int ex_det3(const Ex2* r0, const Ex2* r1, const Ex2* r2, double* out,
+static __device__ __noinline__ int ex_det3(const Ex2* r0, const Ex2* r1, const Ex2* r2, double* out,
                                     bool& bad) {
   double m[16], t[64], tmp[4];
   int n = 1;
@@ -200,7 +200,7 @@ __device__ __noinline__ int ex_det3(const Ex2* r0, const Ex2* r1, const Ex2* r2,
   return ex_compress(out, n);
 }
 
-__device__ __noinline__ int orient3d_exact(Pt a, Pt b, Pt c, Pt d,
+static __device__ __noinline__ int orient3d_exact(Pt a, Pt b, Pt c, Pt d,
                                            DevState* st) {
   atomicAdd(&st->n_exact, 1ull);
   bool bad = false;
@@ -213,7 +213,7 @@ __device__ __noinline__ int orient3d_exact(Pt a, Pt b, Pt c, Pt d,
   return ex_sign(det, n);
 }
 
-__device__ __noinline__ int insphere_exact(Pt a, Pt b, Pt c, Pt d, Pt e,
+static __device__ __noinline__ int insphere_exact(Pt a, Pt b, Pt c, Pt d, Pt e,
                                            DevState* st) {
   atomicAdd(&st->n_exact, 1ull);
   bool bad = false;
@@ -269,7 +269,7 @@ __device__ __noinline__ int insphere_exact(Pt a, Pt b, Pt c, Pt d, Pt e,
 }
 
 // Exact test that c lies on the line ab: every component of (b-a) x (c-a) is zero.
-__device__ __noinline__ bool collinear_exact(Pt a, Pt b, Pt c, DevState* st) {
+static __device__ __noinline__ bool collinear_exact(Pt a, Pt b, Pt c, DevState* st) {
   bool bad = false;
   Ex2 u[3] = {ex_diff(b.x, a.x), ex_diff(b.y, a.y), ex_diff(b.z, a.z)};
   Ex2 v[3] = {ex_diff(c.x, a.x), ex_diff(c.y, a.y), ex_diff(c.z, a.z)};

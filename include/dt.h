@@ -98,7 +98,8 @@ typedef struct {
   uint64_t batch_warps;    /* dt_batch: block shape used (warps per block, autotuned) */
   double batch_alpha;      /* dt_batch: concurrent insertions per mesh vertex used (autotuned) */
   double ms_batch_tune;    /* dt_batch: host time of the autotuning in the last call (0 = reused) */
-  uint64_t reserved[4];
+  uint64_t batch_graph;    /* dt_batch: 1 if the last call replayed its captured CUDA graph */
+  uint64_t reserved[3];
 } dt_stats;
 
 typedef struct dt_handle dt_handle;

@@ -54,14 +54,15 @@ class Stats(ctypes.Structure):
                    ("free_slots", ctypes.c_uint64), ("max_walk", ctypes.c_uint64),
                    ("n_clouds_degenerate", ctypes.c_uint64), ("batch_warps", ctypes.c_uint64),
                    ("batch_alpha", ctypes.c_double), ("ms_batch_tune", ctypes.c_double),
-                   ("reserved", ctypes.c_uint64 * 4)])
+                   ("batch_graph", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)])
 
     def as_dict(self):
         d = {f: getattr(self, f) for f in _STAT_FIELDS}
         for f in ("ms_sort", "ms_insert", "n_launches", "ms_walk", "ms_cavity", "ms_insert_k",
                   "n_profiled", "device_error", "device_error_info", "n_rounds_wave",
                   "n_rounds_retry", "n_rounds_big", "ms_first_round", "n_walk_limit", "free_slots",
-                  "max_walk", "n_clouds_degenerate", "batch_warps", "batch_alpha", "ms_batch_tune"):
+                  "max_walk", "n_clouds_degenerate", "batch_warps", "batch_alpha", "ms_batch_tune",
+                  "batch_graph"):
             d[f] = getattr(self, f)
         return d
 

@@ -51,6 +51,7 @@ struct BatchArgs {
   size_t wsstride;
   float alpha;
   double gamma;            // wave growth: must equal the ordering's, bit for bit
+  const float* eta;        // FP32 stage error term of this batch (computed on the device)
   unsigned long long* stats;  // kBatchStatSlots accumulators
 };
 
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(Ctx c0, BatchArgs a) {
   carve(base + (size_t)wid * a.wsstride, kBatchHashN, kBatchCN, kBatchFN, kBatchEdgeN, &ws);
   carve(base, W * kBatchHashN, W * kBatchCN, W * kBatchFN, W * kBatchEdgeN, &wide);
   DevState* st = a.states + blockIdx.x;
+  const float eta = *a.eta;
   if (tid < kBatchStats) sh.stat[tid] = 0;
   for (;;) {
     __syncthreads();
@@ -252,6 +254,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(Ctx c0, BatchArgs a) {
     BatchCloud* cl = a.clouds + ci;
     const uint32_t vb = cl->vb, ve = cl->ve, tb = cl->tb;
     Ctx c = c0;
+    c.eta = eta;
     c.st = st;
     c.freelist = c0.freelist + tb;
     c.pending = c0.pending + tb;
@@ -439,6 +442,31 @@ __global__ void k_batch_tet_keys(const uint4* tets, uint64_t T, const unsigned l
   }
 }
 
+
+// Hint grid of every cloud (8 cells per axis over its box) and the batch's FP32 error term
+// eta = 2^-44 max|x| (+ the spacing of FP32 subnormals), as the single-cloud engine sets it.
+__global__ void k_batch_prepare(BatchCloud* clouds, const double* __restrict__ cbox, uint32_t n_clouds,
+                                float* eta) {
+  __shared__ double s_max[256];
+  double m = 0.0;
+  for (uint32_t c = threadIdx.x; c < n_clouds; c += blockDim.x) {
+    const double* B = cbox + 6ull * c;
+    for (int k = 0; k < 6; ++k) m = fmax(m, fabs(B[k]));
+    for (int k = 0; k < 3; ++k) {
+      double ext = B[3 + k] - B[k];
+      clouds[c].lo[k] = (float)B[k];
+      clouds[c].sc[k] = ext > 0 ? (float)((double)(1u << kBatchCb) / ext) : 0.f;
+    }
+  }
+  s_max[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *eta = (float)(ldexp(s_max[0], -44) * 1.0001 + 1e-38);
+}
+
 }  // namespace
 
 size_t batch_ws_stride() { return carve(nullptr, kBatchHashN, kBatchCN, kBatchFN, kBatchEdgeN, nullptr); }
@@ -471,9 +499,9 @@ int batch_blocks_per_sm(int W) {
 int batch_launch(int W, unsigned blocks, const Ctx& c, BatchCloud* clouds, const uint32_t* order, uint32_t n_clouds,
                  unsigned int* next, uint8_t* vflag, uint32_t* list_a, uint32_t* list_b, uint32_t* list_big,
                  uint32_t* hint_fine, uint32_t* hint_coarse, DevState* states, char* wsmem, size_t wsstride,
-                 float alpha, double gamma, unsigned long long* stats, cudaStream_t s) {
+                 float alpha, double gamma, const float* eta, unsigned long long* stats, cudaStream_t s) {
   BatchArgs a{clouds, order, n_clouds, next, vflag, list_a, list_b, list_big, hint_fine, hint_coarse, states,
-              wsmem, wsstride, alpha, gamma, stats};
+              wsmem, wsstride, alpha, gamma, eta, stats};
   switch (W) {
     case 4: k_batch<4><<<blocks, 4 * 32, 0, s>>>(c, a); break;
     case 8: k_batch<8><<<blocks, 8 * 32, 0, s>>>(c, a); break;
@@ -491,6 +519,11 @@ void batch_reset(const BatchCloud* clouds, const uint32_t* list, uint32_t n_list
   if (n_list == 0) return;
   k_batch_reset<<<std::min<uint32_t>(n_list, 152u * 8), 256, 0, s>>>(clouds, list, n_list, claim, hint_fine,
                                                                      hint_coarse, dup_sorted, vflag, point_hint);
+  ++g_kernel_launches;
+}
+
+void batch_prepare(BatchCloud* clouds, const double* cbox, uint32_t n_clouds, float* eta, cudaStream_t s) {
+  k_batch_prepare<<<1, 256, 0, s>>>(clouds, cbox, n_clouds, eta);
   ++g_kernel_launches;
 }
 

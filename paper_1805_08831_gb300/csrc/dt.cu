@@ -701,6 +701,14 @@ struct dt_handle {
   float batch_alpha = 0.f;                  // autotuned concurrent insertions per mesh vertex
   uint64_t batch_sig = 0;                   // workload signature the tuning belongs to
   double batch_tune_ms = 0.0;
+  float* beta = nullptr;                    // device: the batch's FP32 error term
+  cudaStream_t bs = nullptr;                // the handle's own stream for batches (capturable)
+  cudaEvent_t bev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraph_t bgraph = nullptr;             // the captured steady-state batch
+  cudaGraphExec_t bexec = nullptr;
+  uint64_t bgraph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint64_t bgraph_kernels = 0;              // kernels in the captured graph
+  bool bgraph_used = false;                 // the last batch replayed the graph
 };
 
 namespace {
@@ -1209,53 +1217,68 @@ Ctx batch_ctx(dt_handle* h) {
   return c;
 }
 
-// One persistent launch over order[0 .. n) with block shape W; returns its device time (ms) or
-// a negative value when the launch failed.
-float batch_run(dt_handle* h, int W, float alpha, const uint32_t* order, uint32_t n, bool reset_all) {
-  cudaStream_t s = h->stream;
+// Batched S1..S4, the vertex records and the per-cloud hint grids: enqueued on the batch stream,
+// no host synchronisation.
+void batch_enqueue_prepare(dt_handle* h, const double* xyz, cudaStream_t s) {
+  const uint64_t N = h->boff[h->n_clouds];
+  cudaMemsetAsync(h->ows.bad, 0, 4, s);
+  order_batch(xyz, N, h->boff_dev, h->n_clouds, h->cfg.seed, h->gamma, h->ows, h->bcid, h->bcbox, s);
+  k_build_pts<<<grid_for(N, 256), 256, 0, s>>>(xyz, h->ows.perm, h->ows.dup, N, 0, h->pts, h->ptf, h->vflag,
+                                                h->point_hint);
+  ++g_kernel_launches;
+  cudaMemcpyAsync(h->bdup, h->vflag, N, cudaMemcpyDeviceToDevice, s);
+  batch_prepare(h->bclouds, h->bcbox, h->n_clouds, h->beta, s);
+}
+
+// Reset of the clouds and the persistent launch over order[0 .. n) with block shape W.
+int batch_enqueue_insert(dt_handle* h, int W, float alpha, const uint32_t* order, uint32_t n, bool reset_all,
+                         cudaStream_t s) {
   batch_reset(h->bclouds, reset_all ? nullptr : order, reset_all ? h->n_clouds : n, h->claim, h->bhint_f, h->bhint_c,
               h->bdup, h->vflag, h->point_hint, s);
   cudaMemsetAsync(h->bnext, 0, 4, s);
   cudaMemsetAsync(h->bstats, 0, kBatchStatSlots * 8, s);
   const unsigned blocks = (unsigned)std::max(1, batch_blocks_per_sm(W)) * (unsigned)sm_count();
-  cudaEventRecord(h->ev[3], s);
-  int rc = batch_launch(W, std::min<unsigned>(blocks, n), batch_ctx(h), h->bclouds, order, n, h->bnext, h->vflag,
-                        h->blist_a, h->blist_b, h->blist_big, h->bhint_f, h->bhint_c, h->bstates, h->bws,
-                        batch_ws_stride(), alpha, h->gamma, h->bstats, s);
-  cudaEventRecord(h->ev[4], s);
+  return batch_launch(W, std::min<unsigned>(blocks, n), batch_ctx(h), h->bclouds, order, n, h->bnext, h->vflag,
+                      h->blist_a, h->blist_b, h->blist_big, h->bhint_f, h->bhint_c, h->bstates, h->bws,
+                      batch_ws_stride(), alpha, h->gamma, h->beta, h->bstats, s);
+}
+
+// One timed launch over order[0 .. n) (the autotuner's trials); device ms, or < 0 on failure.
+float batch_run(dt_handle* h, int W, float alpha, const uint32_t* order, uint32_t n, bool reset_all) {
+  cudaStream_t s = h->bs;
+  cudaEventRecord(h->bev[2], s);
+  int rc = batch_enqueue_insert(h, W, alpha, order, n, reset_all, s);
+  cudaEventRecord(h->bev[3], s);
   if (rc != DT_OK || cudaStreamSynchronize(s) != cudaSuccess) return -1.f;
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]);
+  cudaEventElapsedTime(&ms, h->bev[2], h->bev[3]);
   return ms;
 }
 
 // Autotuner: block shape (warps per block) and round size (concurrent insertions per mesh
 // vertex) timed on a sample of the clouds spread over the size order; the fastest is kept for
 // batches with the same signature (cloud count and size range).
-int batch_tune(dt_handle* h, const std::vector<uint32_t>& by_size) {
+int batch_tune(dt_handle* h, const std::vector<uint32_t>& by_size, uint64_t sig) {
   const uint32_t nc = h->n_clouds;
-  uint64_t big = h->boff[by_size[0] + 1] - h->boff[by_size[0]];
-  uint64_t sig = ((uint64_t)nc << 40) ^ ((uint64_t)(64 - __builtin_clzll(h->boff[nc] | 1)) << 32) ^
-                 (uint64_t)(64 - __builtin_clzll(big | 1));
   const char* fw = std::getenv("DT_BATCH_WARPS");
   const char* fa = std::getenv("DT_BATCH_ALPHA");
+  h->batch_tune_ms = 0.0;
   if (fw && fa) {
     h->batch_W = std::atoi(fw);
     h->batch_alpha = (float)std::atof(fa);
     h->batch_sig = sig;
     return DT_OK;
   }
-  if (h->batch_W && h->batch_sig == sig) return DT_OK;
   // the sample: every k-th cloud of the size order, enough to fill the GPU a few times
   const uint32_t want = std::min<uint32_t>(nc, std::max<uint32_t>(4u * (uint32_t)sm_count(), nc / 8));
   const uint32_t step = std::max<uint32_t>(1, nc / std::max<uint32_t>(want, 1));
   std::vector<uint32_t> sample;
   for (uint32_t k = 0; k < nc && sample.size() < want; k += step) sample.push_back(by_size[k]);
-  if (cudaMemcpyAsync(h->bsample, sample.data(), sample.size() * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(h->bsample, sample.data(), sample.size() * 4, cudaMemcpyHostToDevice, h->bs) != cudaSuccess)
     return DT_ECUDA;
   int shapes[8];
   int ns = batch_shapes(shapes, 8);
-  static const float kAlphas[] = {0.1f, 0.3f};
+  static const float kAlphas[] = {0.1f, 0.3f, 1.0f};
   float best = -1.f;
   auto t0 = std::chrono::steady_clock::now();
   for (int i = 0; i < ns; ++i) {
@@ -1277,12 +1300,11 @@ int batch_tune(dt_handle* h, const std::vector<uint32_t>& by_size) {
 }
 
 int batch_impl(dt_handle* h, const double* xyz, const uint64_t* off, uint32_t nc) {
-  cudaStream_t s = h->stream;
   const uint64_t N = off[nc];
   double f = h->cfg.tet_capacity_factor > 0 ? h->cfg.tet_capacity_factor : 8.0;
   // slots per cloud: f per point plus room for the first tetrahedra and ghosts
   std::vector<BatchCloud> cl(nc);
-  uint64_t T = 0;
+  uint64_t T = 0, hash = 1469598103934665603ull;
   for (uint32_t c = 0; c < nc; ++c) {
     uint64_t n = off[c + 1] - off[c];
     uint64_t cap = (uint64_t)(f * (double)n) + 64;
@@ -1292,54 +1314,107 @@ int batch_impl(dt_handle* h, const double* xyz, const uint64_t* off, uint32_t nc
     cl[c].tb = (uint32_t)T;
     cl[c].tcap = (uint32_t)cap;
     T += cap;
+    hash = (hash ^ n) * 1099511628211ull;
   }
   if (T > 0x3FFFFFFFull) return DT_ENOMEM;  // 4 t + facet must fit 32 bits
   int rc = batch_reserve(h, N, nc, T);
   if (rc != DT_OK) return rc;
+  if (!h->bs) {
+    if (cudaStreamCreateWithFlags(&h->bs, cudaStreamNonBlocking) != cudaSuccess) return DT_ECUDA;
+    for (auto& e : h->bev)
+      if (cudaEventCreate(&e) != cudaSuccess) return DT_ECUDA;
+    if (cudaMalloc(&h->beta, sizeof(float)) != cudaSuccess) return DT_ENOMEM;
+  }
+  cudaStream_t s = h->bs;
+  // the batch stream starts after the caller's stream has produced the input
+  cudaEventRecord(h->bev[0], h->stream);
+  cudaStreamWaitEvent(s, h->bev[0], 0);
   h->n_clouds = nc;
   h->boff.assign(off, off + nc + 1);
-  if (cudaMemcpyAsync(h->boff_dev, off, (nc + 1) * 8ull, cudaMemcpyHostToDevice, s) != cudaSuccess) return DT_ECUDA;
-  cudaEventRecord(h->ev[0], s);
-  if ((rc = order_batch(xyz, N, h->boff_dev, nc, h->cfg.seed, h->gamma, h->ows, h->bcid, h->bcbox, s)) != DT_OK)
-    return rc;
-  k_build_pts<<<grid_for(N, 256), 256, 0, s>>>(xyz, h->ows.perm, h->ows.dup, N, 0, h->pts, h->ptf, h->vflag,
-                                                h->point_hint);
-  ++g_kernel_launches;
-  cudaMemcpyAsync(h->bdup, h->vflag, N, cudaMemcpyDeviceToDevice, s);
-  cudaEventRecord(h->ev[1], s);
-  std::vector<double> box(6ull * nc);
-  if (cudaMemcpyAsync(box.data(), h->bcbox, 48ull * nc, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DT_ECUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
-  h->cmax = 0.0;
-  const double cells = (double)(1u << batch_cb());
-  for (uint32_t c = 0; c < nc; ++c) {
-    for (int k = 0; k < 6; ++k) h->cmax = std::max(h->cmax, std::fabs(box[6ull * c + k]));
-    for (int k = 0; k < 3; ++k) {
-      double ext = box[6ull * c + 3 + k] - box[6ull * c + k];
-      cl[c].lo[k] = (float)box[6ull * c + k];
-      cl[c].sc[k] = ext > 0 ? (float)(cells / ext) : 0.f;
-    }
-  }
   std::vector<uint32_t> by_size(nc);
   for (uint32_t c = 0; c < nc; ++c) by_size[c] = c;
   std::stable_sort(by_size.begin(), by_size.end(), [&](uint32_t a, uint32_t b) {
     return off[a + 1] - off[a] > off[b + 1] - off[b];
   });
-  cudaMemcpyAsync(h->bclouds, cl.data(), nc * sizeof(BatchCloud), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(h->border, by_size.data(), nc * 4ull, cudaMemcpyHostToDevice, s);
+  if (cudaMemcpyAsync(h->boff_dev, off, (nc + 1) * 8ull, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->bclouds, cl.data(), nc * sizeof(BatchCloud), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->border, by_size.data(), nc * 4ull, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return DT_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;  // host vectors go out of scope
   h->n_pts = N;
   h->batch_mode = true;
-  if ((rc = batch_tune(h, by_size)) != DT_OK) return rc;
-  float ms = batch_run(h, h->batch_W, h->batch_alpha, h->border, nc, true);
-  if (ms < 0.f) return DT_ECUDA;
+  unsigned int bad = 0;
+  // the autotuner needs the ordered points: prepare once eagerly, then time the candidates
+  uint64_t big = off[by_size[0] + 1] - off[by_size[0]];
+  uint64_t sig = ((uint64_t)nc << 40) ^ ((uint64_t)(64 - __builtin_clzll(N | 1)) << 32) ^
+                 (uint64_t)(64 - __builtin_clzll(big | 1));
+  bool fixed = std::getenv("DT_BATCH_WARPS") && std::getenv("DT_BATCH_ALPHA");
+  if (fixed || !h->batch_W || h->batch_sig != sig) {
+    batch_enqueue_prepare(h, xyz, s);
+    cudaMemcpyAsync(&bad, h->ows.bad, 4, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
+    if (bad) return DT_EINVAL;
+    if ((rc = batch_tune(h, by_size, sig)) != DT_OK) return rc;
+  } else {
+    h->batch_tune_ms = 0.0;
+  }
+  // the steady state: sort, records, reset and the persistent launch, replayed from a CUDA graph
+  // while the batch keeps its shape (same input buffer, cloud sizes, block shape and round size)
+  const uint64_t key[8] = {(uint64_t)(uintptr_t)xyz, N, nc, hash, (uint64_t)h->batch_W,
+                           (uint64_t)(h->batch_alpha * 1e6f), h->cfg.seed, (uint64_t)(h->gamma * 1e9)};
+  const bool use_graph = !std::getenv("DT_BATCH_NO_GRAPH");
+  h->bgraph_used = false;
+  if (use_graph && !(h->bexec && std::equal(key, key + 8, h->bgraph_key))) {
+    if (h->bexec) cudaGraphExecDestroy(h->bexec);
+    if (h->bgraph) cudaGraphDestroy(h->bgraph);
+    h->bexec = nullptr;
+    h->bgraph = nullptr;
+    unsigned long long k0 = g_kernel_launches;
+    bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      // external records: the graph itself records the events, so every replay is timed
+      cudaEventRecordWithFlags(h->bev[1], s, cudaEventRecordExternal);
+      batch_enqueue_prepare(h, xyz, s);
+      cudaEventRecordWithFlags(h->bev[2], s, cudaEventRecordExternal);
+      int rl = batch_enqueue_insert(h, h->batch_W, h->batch_alpha, h->border, nc, true, s);
+      cudaEventRecordWithFlags(h->bev[3], s, cudaEventRecordExternal);
+      ok = cudaStreamEndCapture(s, &h->bgraph) == cudaSuccess && rl == DT_OK;
+    }
+    if (ok) ok = cudaGraphInstantiate(&h->bexec, h->bgraph, 0) == cudaSuccess;
+    if (ok) {
+      std::copy(key, key + 8, h->bgraph_key);
+      h->bgraph_kernels = g_kernel_launches - k0;
+    } else {
+      cudaGetLastError();  // capture unsupported here: run the same sequence eagerly
+      if (h->bgraph) cudaGraphDestroy(h->bgraph);
+      h->bgraph = nullptr;
+      h->bexec = nullptr;
+    }
+    g_kernel_launches = k0;
+  }
+  if (use_graph && h->bexec) {
+    if (cudaGraphLaunch(h->bexec, s) != cudaSuccess) return DT_ECUDA;
+    g_kernel_launches += h->bgraph_kernels;
+    h->bgraph_used = true;
+  } else {
+    cudaEventRecord(h->bev[1], s);
+    batch_enqueue_prepare(h, xyz, s);
+    cudaEventRecord(h->bev[2], s);
+    if ((rc = batch_enqueue_insert(h, h->batch_W, h->batch_alpha, h->border, nc, true, s)) != DT_OK) return rc;
+    cudaEventRecord(h->bev[3], s);
+  }
   // results: per-cloud status and sizes, and the batch counters
   h->bclouds_host.resize(nc);
   unsigned long long st[kBatchStatSlots];
+  cudaMemcpyAsync(&bad, h->ows.bad, 4, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(h->bclouds_host.data(), h->bclouds, nc * sizeof(BatchCloud), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(st, h->bstats, sizeof(st), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
-  float ms_sort = 0.f;
-  cudaEventElapsedTime(&ms_sort, h->ev[0], h->ev[1]);
+  if (bad) return DT_EINVAL;
+  float ms_sort = 0.f, ms_ins = 0.f;
+  if (cudaEventElapsedTime(&ms_sort, h->bev[1], h->bev[2]) != cudaSuccess) ms_sort = 0.f;
+  if (cudaEventElapsedTime(&ms_ins, h->bev[2], h->bev[3]) != cudaSuccess) ms_ins = 0.f;
+  cudaGetLastError();
   DevState agg{};
   uint64_t degenerate = 0, used = 0;
   for (const BatchCloud& b : h->bclouds_host) {
@@ -1363,13 +1438,14 @@ int batch_impl(dt_handle* h, const double* xyz, const uint64_t* off, uint32_t nc
   agg.bump = used;
   std::memcpy(h->st_host, &agg, sizeof(agg));
   h->stats.ms_sort = ms_sort;
-  h->stats.ms_insert = ms;
+  h->stats.ms_insert = ms_ins;
   h->stats.n_rounds = st[8];
   h->stats.n_passes = 0;
   h->stats.n_clouds_degenerate = degenerate;
   h->stats.batch_warps = (uint64_t)h->batch_W;
   h->stats.batch_alpha = h->batch_alpha;
   h->stats.ms_batch_tune = h->batch_tune_ms;
+  h->stats.batch_graph = h->bgraph_used ? 1 : 0;
   // DT_EDEGENERATE only when no cloud could be triangulated
   if (h->last_dev_error) return map_dev_error(h->last_dev_error);
   return degenerate == nc ? DT_EDEGENERATE : DT_OK;
@@ -1724,6 +1800,12 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->bws);
   cudaFree(h->bstats);
   cudaFree(h->bnext);
+  cudaFree(h->beta);
+  if (h->bexec) cudaGraphExecDestroy(h->bexec);
+  if (h->bgraph) cudaGraphDestroy(h->bgraph);
+  for (auto& e : h->bev)
+    if (e) cudaEventDestroy(e);
+  if (h->bs) cudaStreamDestroy(h->bs);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->prof_events) cudaEventDestroy(e);

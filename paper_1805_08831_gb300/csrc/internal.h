@@ -102,6 +102,8 @@ int order_points(const double* xyz, uint64_t n, uint64_t seed, OrderWS& ws, cuda
 // by (cloud, round, wave, key, index), so every cloud keeps its input rows' positions and every
 // wave (wave_of with gamma, n0 = the round's first rank) is a contiguous range. cid [n] and
 // cbox [6 n_clouds] (device) receive the cloud of every input index and every cloud's box.
+// Enqueues only (no host synchronisation, so it can be captured into a graph): ws.bad becomes
+// non-zero on a non-finite or |x| > 1e30 coordinate.
 int order_batch(const double* xyz, uint64_t n, const uint64_t* offsets_dev, uint32_t n_clouds, uint64_t seed,
                 double gamma, OrderWS& ws, uint32_t* cid, double* cbox, cudaStream_t s);
 
@@ -135,7 +137,10 @@ constexpr int kBatchStatSlots = 11;      // accumulators batch_launch adds into
 int batch_launch(int W, unsigned blocks, const Ctx& c, BatchCloud* clouds, const uint32_t* order, uint32_t n_clouds,
                  unsigned int* next, uint8_t* vflag, uint32_t* list_a, uint32_t* list_b, uint32_t* list_big,
                  uint32_t* hint_fine, uint32_t* hint_coarse, DevState* states, char* wsmem, size_t wsstride,
-                 float alpha, double gamma, unsigned long long* stats, cudaStream_t s);
+                 float alpha, double gamma, const float* eta, unsigned long long* stats, cudaStream_t s);
+// Per-cloud hint grids from the clouds' boxes cbox [6 n_clouds], and the FP32 stage's error
+// term eta (from the largest |coordinate| of the batch) into *eta, on the device.
+void batch_prepare(BatchCloud* clouds, const double* cbox, uint32_t n_clouds, float* eta, cudaStream_t s);
 // Resets the clouds list[0 .. n_list) (all clouds when list is null) for a new launch.
 void batch_reset(const BatchCloud* clouds, const uint32_t* list, uint32_t n_list, unsigned long long* claim,
                  uint32_t* hint_fine, uint32_t* hint_coarse, const uint8_t* dup_sorted, uint8_t* vflag,

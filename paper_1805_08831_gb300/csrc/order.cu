@@ -699,11 +699,7 @@ int order_batch(const double* xyz, uint64_t n, const uint64_t* offsets_dev, uint
   cudaMemcpyAsync(ws.v0, ws.perm, n * 4, cudaMemcpyDeviceToDevice, s);
   bool alt4 = radix_sort_pairs_bits(ws.k0, ws.v0, ws.k1, ws.v1, n, 0, cbits + 16, ws.hist, s);
   cudaMemcpyAsync(ws.perm, alt4 ? ws.v1 : ws.v0, n * 4, cudaMemcpyDeviceToDevice, s);
-  unsigned int bad = 0;
-  cudaMemcpyAsync(&bad, ws.bad, 4, cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
-  if (bad) return DT_EINVAL;
-  return DT_OK;
+  return cudaPeekAtLastError() == cudaSuccess ? DT_OK : DT_ECUDA;
 }
 
 void transformed_keys(const Pt* pts, const uint32_t* ids, uint64_t m, const double* bbox,

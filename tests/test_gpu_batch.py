@@ -119,3 +119,28 @@ def test_batch_at_scale_sampled_clouds():
         x = xyz[int(off[c]):int(off[c + 1])]
         ref, _ = oracle.delaunay(x)
         assert np.array_equal(tets[int(coff[c]):int(coff[c + 1])], ref), c
+
+
+def test_repeated_batch_replays_its_graph_on_new_data():
+    """The second call with the same buffer and cloud sizes replays the captured CUDA graph; the
+    graph computes everything that depends on the coordinates on the device, so new values in
+    the same buffer give their own triangulations."""
+    xyz, off = synth.batched_clouds(30, 41, lo=50, hi=3000)
+    xd = torch.from_numpy(xyz).cuda()
+    with dt.Triangulation(seed=0) as t:
+        t.batch(xd, off)
+        first, c1 = t.tets_batch()
+        t.clear()
+        t.batch(xd, off)
+        again, c2 = t.tets_batch()
+        st = t.stats()
+        assert st["batch_graph"] == 1
+        assert np.array_equal(first, again) and np.array_equal(c1, c2)
+        xyz2 = synth.uniform(99, 3 * len(xyz)).reshape(-1, 3)  # same cloud sizes, new coordinates
+        xd.copy_(torch.from_numpy(xyz2 * 3.0 - 1.0))
+        t.clear()
+        t.batch(xd, off)
+        new, c3 = t.tets_batch()
+        assert t.stats()["batch_graph"] == 1
+    clouds = split(xyz2 * 3.0 - 1.0, off)
+    assert_clouds_match(clouds, [new[int(c3[c]):int(c3[c + 1])] for c in range(30)])

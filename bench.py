@@ -39,7 +39,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=float, default=1e7)
-    ap.add_argument("--kind", default="uniform", choices=["uniform", "slab", "degenerate"])
+    ap.add_argument("--kind", default="uniform", choices=["uniform", "slab", "degenerate", "batch"])
+    ap.add_argument("--clouds", type=int, default=4096, help="clouds of the batch workload")
+    ap.add_argument("--schedule", default="plain", choices=["plain", "learned"],
+                    help="learned: train the scheduler on plain round logs first, then time both")
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--plain-sample", type=int, default=128,
+                    help="clouds timed one dt_insert each for the batch's per-cloud comparison")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=float, default=1e6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -158,14 +164,32 @@ def reference_arm(args, rank):
     if rank != 0:
         return
     n = int(args.n)
-    x_full = synth.make(args.kind, n, SEED)
-    m = int(min(2e5, n))
-    x = np.ascontiguousarray(x_full[:m])
+    if args.kind == "batch":
+        # whole clouds of the batch, in input order, up to about 2e5 points per step
+        xyz, off = synth.batched_clouds(args.clouds, 4)
+        last = int(np.searchsorted(off.astype(np.int64), 200000, side="right"))
+        clouds = [np.ascontiguousarray(xyz[int(off[c]):int(off[c + 1])]) for c in range(max(last - 1, 1))]
+        m = sum(len(c) for c in clouds)
+
+        def step():
+            tot, tt = 0, 0.0
+            for c in clouds:
+                k, t = run_oracle(c, SEED)
+                tot += k
+                tt += t
+            return tot, tt
+    else:
+        x_full = synth.make(args.kind, n, SEED)
+        m = int(min(2e5, n))
+        x = np.ascontiguousarray(x_full[:m])
+
+        def step():
+            return run_oracle(x, SEED)
     for _ in range(args.warmup):
-        run_oracle(x, SEED)
+        step()
     times, ntet = [], 0
     for _ in range(args.steps):
-        ntet, t = run_oracle(x, SEED)
+        ntet, t = step()
         times.append(t)
     v = ntet * len(times) / sum(times) / 1e6
     line = {
@@ -173,12 +197,162 @@ def reference_arm(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.kind, args.n), "sample_points": m},
+        "config": {"workload": batch_workload_name(args.clouds) if args.kind == "batch"
+                   else workload_name(args.kind, args.n), "sample_points": m},
         "cpu_baseline": {"value": v, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {m} points of the workload per step"},
         "e2e": {"value": v, "unit": "Mtets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def batch_workload_name(n_clouds):
+    return (f"{n_clouds} independent clouds, sizes log-uniform in [50, 50000], each i.i.d. uniform "
+            f"in its own unit cube, float64, seed 4")
+
+
+def main_batch(args, rank, world, local):
+    """Batched workload: all clouds in one dt_batch call (one persistent graph-replayed launch)
+    against one plain dt_insert launch sequence per cloud on a sample of the clouds."""
+    import torch
+    import paper_1805_08831_gb300 as dt
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    xyz, off = synth.batched_clouds(args.clouds, 4 + rank)
+    xd = torch.from_numpy(xyz).cuda()
+    stream = torch.cuda.current_stream()
+    tri = dt.Triangulation(seed=SEED, stream=stream)
+    for _ in range(max(args.warmup, 1)):  # the first call tunes the block shape and captures the graph
+        tri.clear()
+        tri.batch(xd, off)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    step_ms, st = [], None
+    with ClockSampler(local) as clk:
+        barrier()
+        for _ in range(args.steps):
+            tri.clear()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tri.batch(xd, off)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            st = tri.stats()
+        barrier()
+    clocks = clk.summary()
+    ntet = tri.num_tets()
+    mine = np.array([sum(step_ms), float(ntet)], dtype=np.float64)
+    if dist is not None:
+        t = torch.tensor(mine, device="cuda")
+        tmax, tsum = t.clone(), t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, all_tets = float(tmax[0]), float(tsum[1])
+    else:
+        total_ms, all_tets = float(mine[0]), float(mine[1])
+    value = all_tets * args.steps / (total_ms / 1e3) / 1e6
+
+    # the same clouds one dt_insert each (a full launch sequence per cloud), on a sample spread
+    # over the size order, weighted back to the whole batch by points
+    sizes = np.diff(off.astype(np.int64))
+    order = np.argsort(-sizes, kind="stable")
+    k = max(1, len(order) // max(args.plain_sample, 1))
+    sample = order[::k][: args.plain_sample]
+    plain_ms, plain_tets = 0.0, 0
+    single = dt.Triangulation(seed=SEED, stream=stream)
+    for c in sample:
+        xc = xd[int(off[c]):int(off[c + 1])]
+        single.clear()
+        single.insert(xc)  # warm (allocations)
+        single.clear()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        single.insert(xc)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        plain_tets += single.num_tets()
+    single.close()
+    plain_value = plain_tets / (plain_ms / 1e3) / 1e6
+
+    # end to end: pinned host input copied in and tetrahedra copied out inside the timed region
+    pinned = torch.from_numpy(xyz).pin_memory()
+    e2e_ms, T = [], 0
+    for _ in range(max(args.e2e_steps, 0)):
+        tri.clear()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd.copy_(pinned, non_blocking=True)
+        tri.batch(xd, off)
+        tets, coff = tri.tets_batch(canonical=False)
+        t1 = time.perf_counter()
+        T = len(tets)
+        e2e_ms.append(1e3 * (t1 - t0))
+    e2e_value = T / (statistics.median(e2e_ms) / 1e3) / 1e6 if e2e_ms else None
+
+    peak, peak_kind = load_peaks()
+    bytes_k, cfb = kernel_bytes(st)
+    alg = sum(bytes_k.values())
+    achieved = alg / (st["ms_insert"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mtets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": batch_workload_name(args.clouds), "n_clouds": args.clouds,
+                   "n_points": int(off[-1]), "tets": ntet, "schedule": "batched",
+                   "l2": "inputs and tetrahedron store larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "batch_warps": st["batch_warps"], "batch_min_blocks": st["batch_min_blocks"],
+                   "batch_alpha": st["batch_alpha"], "ms_tune": st["ms_batch_tune"],
+                   "graph_replay": st["batch_graph"], "ms_sort": st["ms_sort"], "ms_insert": st["ms_insert"],
+                   "stats": {k: st[k] for k in ("n_rounds", "n_attempts", "n_conflicts", "n_big", "n_exact",
+                                                 "n_sos", "sum_walk")},
+                   "mean_C": cfb["C"], "mean_F": cfb["F"]},
+        "plain_per_cloud": {"value": plain_value, "unit": "Mtets/s", "clouds_timed": len(sample),
+                            "how": "one dt_insert (its full launch sequence) per cloud, device time, "
+                                   "clouds spread over the size order"},
+        "batched_over_plain": value / plain_value if plain_value else None,
+        "e2e": {"value": e2e_value, "unit": "Mtets/s", "h2d_bytes_per_step": int(off[-1]) * 24,
+                "d2h_bytes_per_step": T * 16, "ms": statistics.median(e2e_ms) if e2e_ms else None},
+        "gpu_launches": int(st["n_launches"]),
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                     "alg_bytes_per_launch": alg, "ms_per_launch": st["ms_insert"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on whole clouds of the sample until about 15 s of CPU work
+        import oracle
+        t_cpu, n_cpu, used = 0.0, 0, 0
+        for c in sample[::-1]:
+            x = np.ascontiguousarray(xyz[int(off[c]):int(off[c + 1])])
+            t0 = time.perf_counter()
+            tets_c, _ = oracle.delaunay(x, seed=SEED)
+            t_cpu += time.perf_counter() - t0
+            n_cpu += len(tets_c)
+            used += 1
+            if t_cpu > 15.0:
+                break
+        line["cpu_baseline"] = {"value": n_cpu / t_cpu / 1e6, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{used} whole clouds of the batch, serial CPU oracle, "
+                                          f"{n_cpu} tetrahedra in {t_cpu:.2f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tri.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
@@ -188,6 +362,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank)
+        return
+    if args.kind == "batch":
+        main_batch(args, rank, world, local)
         return
     import torch
     import paper_1805_08831_gb300 as dt
@@ -202,7 +379,44 @@ def main():
     xd = torch.from_numpy(x_host).cuda()
     stream = torch.cuda.current_stream()
     flags = 0 if args.no_profile else dt.DT_FLAG_PROFILE
-    tri = dt.Triangulation(seed=SEED, stream=stream, flags=flags)
+    learned_info = None
+    if args.schedule == "learned":
+        # the scheduler is trained on the GPU on round logs of the plain schedule (small versions
+        # of the uniform, degenerate and slab workloads), then the same cloud runs both ways
+        from paper_1805_08831_gb300 import learned
+        t0 = time.perf_counter()
+        params, losses = learned.train_scheduler(
+            [synth.uniform_cube(100000, 1), synth.uniform_cube(1000000, 11), synth.degenerate_mix(1000000, 3),
+             synth.cube_and_slab(1000000, 5)], steps=args.train_steps)
+        train_s = time.perf_counter() - t0
+        plain = dt.Triangulation(seed=SEED, stream=stream, flags=flags)
+        for _ in range(max(1, args.warmup)):
+            plain.clear()
+            plain.insert(xd)
+        torch.cuda.synchronize()
+        p_ms, p_st = [], None
+        for _ in range(args.steps):
+            plain.clear()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plain.insert(xd)
+            e1.record(stream)
+            e1.synchronize()
+            p_ms.append(e0.elapsed_time(e1))
+            p_st = plain.stats()
+        p_tets = plain.num_tets()
+        plain.close()
+        learned_info = {"train_s": train_s, "train_steps": args.train_steps,
+                        "train_loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())],
+                        "plain": {"value": p_tets * len(p_ms) / (sum(p_ms) / 1e3) / 1e6, "unit": "Mtets/s",
+                                  "ms_per_step": sum(p_ms) / len(p_ms), "n_conflicts": p_st["n_conflicts"],
+                                  "n_attempts": p_st["n_attempts"], "n_rounds": p_st["n_rounds"],
+                                  "n_passes": p_st["n_passes"]}}
+    tri = dt.Triangulation(seed=SEED, stream=stream, flags=flags,
+                           schedule=dt.DT_SCHED_LEARNED if args.schedule == "learned" else dt.DT_SCHED_PLAIN)
+    if args.schedule == "learned":
+        tri.load_model(params)
     for _ in range(args.warmup):
         tri.clear()
         tri.insert(xd)
@@ -293,7 +507,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_1E7_EPYC if (args.kind == "uniform" and n == 10**7) else None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.kind, n), "n_points": n, "schedule": "plain",
+        "config": {"workload": workload_name(args.kind, n), "n_points": n, "schedule": args.schedule,
                    "tets": ntet, "l2": "inputs and tetrahedron store larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "baseline_ref": "paper Fig. 9, AMD EPYC 7551, 1e7 uniform: 31.3 Mtets/s",
@@ -310,6 +524,9 @@ def main():
         "clocks": clocks,
         "roofline": roofline,
     }
+    if learned_info is not None:
+        learned_info["learned_over_plain"] = value / learned_info["plain"]["value"]
+        line["learned"] = learned_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(x_host, args.cpu_sample)
     if rank == 0:

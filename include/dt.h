@@ -50,6 +50,11 @@ extern "C" {
 
 #define DT_FLAG_NO_CANONICAL_SORT 1u /* dt_get_tets(canonical=1) rotates but does not sort */
 #define DT_FLAG_PROFILE 2u           /* time each launch of the round kernels with CUDA events */
+#define DT_FLAG_LOG 4u               /* log per point: cavity size of its insertion, conflicts lost
+                                        (the learned scheduler's training labels, dt_get_features) */
+
+#define DT_MLP_PARAMS 1410u          /* parameters of the learned scheduler's network */
+#define DT_FEATURES 8u               /* inputs per point */
 
 typedef struct {
   double tet_capacity_factor; /* tetrahedron slots reserved per point; 0 = 8.0 */
@@ -99,7 +104,8 @@ typedef struct {
   double batch_alpha;      /* dt_batch: concurrent insertions per mesh vertex used (autotuned) */
   double ms_batch_tune;    /* dt_batch: host time of the autotuning in the last call (0 = reused) */
   uint64_t batch_graph;    /* dt_batch: 1 if the last call replayed its captured CUDA graph */
-  uint64_t reserved[3];
+  uint64_t batch_min_blocks; /* dt_batch: resident blocks per SM the chosen shape was built for */
+  uint64_t reserved[2];
 } dt_stats;
 
 typedef struct dt_handle dt_handle;
@@ -156,8 +162,39 @@ int dt_get_order(dt_handle* h, uint64_t* keys_dev, uint32_t* perm_dev, uint8_t* 
 int dt_get_stats(dt_handle* h, dt_stats* out);
 
 /* Loads the learned scheduler's parameters (float32, host): W1[8x32], b1[32], W2[32x32], b2[32],
- * W3[32x2], b3[2] row-major in that order, n_params = 1410. Used when schedule = LEARNED. */
+ * W3[32x2], b3[2] row-major in that order (W[i][j]: input i -> output j), n_params = 1410.
+ * Used by dt_insert when cfg.schedule = DT_SCHED_LEARNED (DT_ESTATE if none is loaded). The
+ * network maps a point's features (dt_get_features) to out[0] = predicted log2(1 + |C|) and
+ * out[1] = the logit of the probability that the point loses a conflict; points predicted to
+ * have small cavities claim with a higher priority than points expected to have large ones
+ * (conflicts are settled by any strict total order of the points, Section 3.2; a large cavity
+ * that wins knocks out every small one it overlaps, so fewer attempts are lost). The tetrahedra
+ * do not depend on the schedule. */
 int dt_load_model(dt_handle* h, const float* params_host, uint32_t n_params);
+
+/* Per-point features and labels of the last dt_insert call, in insertion order (the order of
+ * dt_get_order's perm): x_dev [n, 8] float32 (device) = log2-scaled point count of the point's
+ * cell of a ~4-points-per-cell grid, the mean / spread of its 6 face neighbours' counts, the
+ * density contrast, two 6-bit fields of the Moore key, the BRIO round / 8 and the distance to
+ * the box boundary (fraction of the half-extent). With DT_FLAG_LOG, y_dev [n, 2] receives the
+ * labels (log2(1 + |C|) of the point's insertion, 1 if it lost a conflict first) and valid_dev
+ * [n] (uint8) 1 where the point was inserted by a concurrent round (0: init, duplicate, or the
+ * label is missing). y_dev and valid_dev may be NULL. n must equal the call's point count. */
+int dt_get_features(dt_handle* h, float* x_dev, float* y_dev, uint8_t* valid_dev, uint64_t n);
+
+/* The network on n feature rows (device): out_dev [n, 2] float32. */
+int dt_mlp_forward(const float* params_dev, const float* x_dev, uint64_t n, float* out_dev, void* stream);
+
+/* Mean loss over n samples, (out0 - y0)^2 + softplus(out1) - y1 * out1, into *loss_dev, and its
+ * gradient with respect to the 1410 parameters into grad_dev (all device, float32). */
+int dt_mlp_grad(const float* params_dev, const float* x_dev, const float* y_dev, uint64_t n, float* grad_dev,
+                float* loss_dev, void* stream);
+
+/* Trains params_dev in place on the GPU: `steps` Adam steps (learning rate lr) on minibatches of
+ * `batch` samples drawn from the n rows by a counter-based hash of (seed, step). losses_host
+ * (may be NULL) receives each step's minibatch loss. */
+int dt_mlp_train(float* params_dev, const float* x_dev, const float* y_dev, uint64_t n, uint32_t steps,
+                 uint32_t batch, float lr, uint64_t seed, float* losses_host, void* stream);
 
 /* Forgets the triangulation and the points but keeps the device memory, so the next dt_insert
  * starts a new triangulation without allocating (used between repeated runs). */

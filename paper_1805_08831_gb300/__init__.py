@@ -21,6 +21,9 @@ DT_OK, DT_EINVAL, DT_ENOMEM, DT_ETOOSMALL, DT_EDEGENERATE, DT_ELIMIT, DT_ECUDA, 
 DT_SCHED_PLAIN, DT_SCHED_LEARNED = 0, 1
 DT_FLAG_NO_CANONICAL_SORT = 1
 DT_FLAG_PROFILE = 2
+DT_FLAG_LOG = 4
+DT_MLP_PARAMS = 1410
+DT_FEATURES = 8
 
 
 class Config(ctypes.Structure):
@@ -54,7 +57,8 @@ class Stats(ctypes.Structure):
                    ("free_slots", ctypes.c_uint64), ("max_walk", ctypes.c_uint64),
                    ("n_clouds_degenerate", ctypes.c_uint64), ("batch_warps", ctypes.c_uint64),
                    ("batch_alpha", ctypes.c_double), ("ms_batch_tune", ctypes.c_double),
-                   ("batch_graph", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)])
+                   ("batch_graph", ctypes.c_uint64), ("batch_min_blocks", ctypes.c_uint64),
+                   ("reserved", ctypes.c_uint64 * 2)])
 
     def as_dict(self):
         d = {f: getattr(self, f) for f in _STAT_FIELDS}
@@ -62,7 +66,7 @@ class Stats(ctypes.Structure):
                   "n_profiled", "device_error", "device_error_info", "n_rounds_wave",
                   "n_rounds_retry", "n_rounds_big", "ms_first_round", "n_walk_limit", "free_slots",
                   "max_walk", "n_clouds_degenerate", "batch_warps", "batch_alpha", "ms_batch_tune",
-                  "batch_graph"):
+                  "batch_graph", "batch_min_blocks"):
             d[f] = getattr(self, f)
         return d
 
@@ -108,6 +112,10 @@ def lib():
         L.dt_strerror.restype = ctypes.c_char_p
         L.dt_eval_predicates.argtypes = [ctypes.c_int, p, p, p, u64, p]
         L.dt_order_noalloc.argtypes = [p, u64, u64, p, p, p, p]
+        L.dt_get_features.argtypes = [p, p, p, p, u64]
+        L.dt_mlp_forward.argtypes = [p, p, u64, p, p]
+        L.dt_mlp_grad.argtypes = [p, p, p, u64, p, p, p]
+        L.dt_mlp_train.argtypes = [p, p, p, u64, u32, u32, ctypes.c_float, u64, p, p]
         for name in exported_names():
             getattr(L, name)
         _lib = L
@@ -264,6 +272,23 @@ class Triangulation:
         return (keys.cpu().numpy().view(np.uint64), perm.cpu().numpy().view(np.uint32),
                 rounds.cpu().numpy())
 
+    def load_model(self, params):
+        """Loads the learned scheduler's 1410 float32 parameters (host array)."""
+        a = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        _check(lib().dt_load_model(self._h, a.ctypes.data_as(ctypes.c_void_p), a.size), "dt_load_model")
+
+    def features(self, n: int, labels: bool = True):
+        """Features [n, 8] of the last insert's points in insertion order (CUDA float32), and
+        with labels=True (needs DT_FLAG_LOG) the labels [n, 2] and their validity [n] (uint8)."""
+        torch = _torch()
+        x = torch.empty((n, DT_FEATURES), dtype=torch.float32, device="cuda")
+        y = torch.empty((n, 2), dtype=torch.float32, device="cuda") if labels else None
+        v = torch.empty(n, dtype=torch.uint8, device="cuda") if labels else None
+        _check(lib().dt_get_features(self._h, ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(y.data_ptr()) if labels else None,
+                                     ctypes.c_void_p(v.data_ptr()) if labels else None, n), "dt_get_features")
+        return (x, y, v) if labels else x
+
     def stats(self) -> dict:
         st = Stats()
         _check(lib().dt_get_stats(self._h, ctypes.byref(st)), "dt_get_stats")
@@ -291,3 +316,42 @@ def eval_predicates(kind: int, pts, ids=None, stream=None):
     _check(lib().dt_eval_predicates(kind, ctypes.c_void_p(pts.data_ptr()), idp, ctypes.c_void_p(out.data_ptr()),
                                     n, _stream_ptr(stream)), "dt_eval_predicates")
     return out
+
+
+def mlp_forward(params, x):
+    """The learned scheduler's network on CUDA float32 rows x [n, 8]: [n, 2]."""
+    torch = _torch()
+    out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+    _check(lib().dt_mlp_forward(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(x.contiguous().data_ptr()),
+                                x.shape[0], ctypes.c_void_p(out.data_ptr()), None), "dt_mlp_forward")
+    return out
+
+
+def mlp_grad(params, x, y):
+    """(mean loss, gradient [1410]) of the network on CUDA float32 samples (x [n, 8], y [n, 2])."""
+    torch = _torch()
+    g = torch.empty(DT_MLP_PARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().dt_mlp_grad(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(x.contiguous().data_ptr()),
+                             ctypes.c_void_p(y.contiguous().data_ptr()), x.shape[0], ctypes.c_void_p(g.data_ptr()),
+                             ctypes.c_void_p(loss.data_ptr()), None), "dt_mlp_grad")
+    return float(loss.item()), g
+
+
+def mlp_train(params, x, y, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
+    """Trains CUDA float32 params [1410] in place with the library's Adam kernels; returns the
+    per-step minibatch losses (numpy)."""
+    losses = np.zeros(max(steps, 1), dtype=np.float32)
+    _check(lib().dt_mlp_train(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(x.contiguous().data_ptr()),
+                              ctypes.c_void_p(y.contiguous().data_ptr()), x.shape[0], steps, batch, lr, seed,
+                              losses.ctypes.data_as(ctypes.c_void_p), None), "dt_mlp_train")
+    return losses[:steps]
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-scaled random initial parameters (float32 [1410]) in the dt_load_model layout."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, np.sqrt(2 / 8), (8, 32)), np.zeros(32), rng.normal(0, np.sqrt(2 / 32), (32, 32)),
+             np.zeros(32), rng.normal(0, np.sqrt(1 / 32), (32, 2)), np.zeros(2)]
+    return np.concatenate([q.ravel() for q in parts]).astype(np.float32)
+

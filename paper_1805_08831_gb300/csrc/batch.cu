@@ -71,7 +71,7 @@ struct BlockShared {
 // rounds of R segments (Section 3.3), segment s offering q[s * L + j] in round j. Losers go to
 // out, large cavities to big.
 template <int W>
-__device__ void batch_pass(Ctx& c, BlockShared<W>& sh, const BigWS& ws, const uint32_t* q, uint32_t qbase,
+__device__ void batch_pass(const Ctx& c, BlockShared<W>& sh, const BigWS& ws, const uint32_t* q, uint32_t qbase,
                            uint64_t m, uint32_t* out, uint32_t* big, uint8_t* vflag, float alpha, bool last_chance) {
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -89,7 +89,7 @@ __device__ void batch_pass(Ctx& c, BlockShared<W>& sh, const BigWS& ws, const ui
   const uint64_t L = sh.L;
   const uint32_t max_walk = last_chance ? kBatchLongWalk : c.max_walk;
   for (uint64_t j = 0; j < L; ++j) {
-    // walk: one thread per candidate
+    // walk: one thread per candidate (the lanes of the first warp walk together)
     if (tid < (int)R) {
       uint64_t idx = (uint64_t)tid * L + j;
       uint32_t status = kCandEmpty, p = kNone, t = kNone;
@@ -119,7 +119,7 @@ __device__ void batch_pass(Ctx& c, BlockShared<W>& sh, const BigWS& ws, const ui
     // cavity and claims: one warp per candidate
     if (wid < (int)R && sh.st[wid] == kCandLocated) {
       uint32_t p = sh.p[wid];
-      unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+      unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), 0u, p);
       int nc = 0, nb = 0;
       int r = cavity_warp(c, ws.cav, sh.t[wid], p, load_ptf(c.ptf, p), prio, &nc, &nb);
       if (lane == 0) {
@@ -130,16 +130,16 @@ __device__ void batch_pass(Ctx& c, BlockShared<W>& sh, const BigWS& ws, const ui
     }
     __threadfence();
     __syncthreads();
-    // ball
-    if (wid < (int)R && sh.st[wid] == kCandLocated) {
-      uint32_t p = sh.p[wid];
-      unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
-      int nc = (int)sh.nc[wid], nb = (int)sh.nb[wid];
-      int r = insert_warp(c, ws.ins, p, prio, ws.cav.clist, nc, ws.cav.blist, nb, nb <= kFMax,
-                          __ldcg(&c.st->free_avail), __ldcg(&c.st->bump), c.st->capacity);
-      if (lane == 0) {
-        sh.st[wid] = (uint32_t)r;
-        if (r == kCandInserted) {
+    // ball, then the candidate's bookkeeping by the same warp
+    if (wid < (int)R) {
+      const uint32_t p = sh.p[wid];
+      uint32_t s = sh.st[wid];
+      if (s == kCandLocated) {
+        unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), 0u, p);
+        int nc = (int)sh.nc[wid], nb = (int)sh.nb[wid];
+        s = (uint32_t)insert_warp(c, ws.ins, p, prio, ws.cav.clist, nc, ws.cav.blist, nb, nb <= kFMax,
+                                  __ldcg(&c.st->free_avail), __ldcg(&c.st->bump), c.st->capacity);
+        if (lane == 0 && s == kCandInserted) {
           PtF FP = load_ptf(c.ptf, p);
           uint32_t f, g, s0 = ws.ins.slot[0];
           cells_of(c, FP, &f, &g);
@@ -154,20 +154,19 @@ __device__ void batch_pass(Ctx& c, BlockShared<W>& sh, const BigWS& ws, const ui
           atomicAdd(&sh.stat[4], (unsigned long long)nb);
         }
       }
+      if (lane == 0) {
+        if (s != kCandEmpty) atomicAdd(&sh.stat[2], 1ull);
+        if (s == kCandLost) atomicAdd(&sh.stat[1], 1ull);
+        if (s == kCandLost || s == kCandWalkLimit) out[atomicAdd(&sh.nout, 1u)] = p;
+        else if (s == kCandBig) big[atomicAdd(&sh.nbig, 1u)] = p;
+        else if (s == kCandDup) {
+          vflag[p] = 1;
+          atomicAdd(&sh.stat[6], 1ull);
+        }
+      }
     }
     __threadfence();
     __syncthreads();
-    if (tid < (int)R) {
-      uint32_t s = sh.st[tid], p = sh.p[tid];
-      if (s != kCandEmpty) atomicAdd(&sh.stat[2], 1ull);
-      if (s == kCandLost) atomicAdd(&sh.stat[1], 1ull);
-      if (s == kCandLost || s == kCandWalkLimit) out[atomicAdd(&sh.nout, 1u)] = p;
-      else if (s == kCandBig) big[atomicAdd(&sh.nbig, 1u)] = p;
-      else if (s == kCandDup) {
-        vflag[p] = 1;
-        atomicAdd(&sh.stat[6], 1ull);
-      }
-    }
     if (tid == 0) sh.stat[8] += 1;
     finish_round_block(c);
   }
@@ -176,7 +175,7 @@ __device__ void batch_pass(Ctx& c, BlockShared<W>& sh, const BigWS& ws, const ui
 // The large cavities of a pass, one at a time by warp 0 with the whole block's workspace (the
 // other warps wait at the barrier that follows).
 template <int W>
-__device__ void batch_big(Ctx& c, BlockShared<W>& sh, const BigWS& wide, uint32_t* big, uint8_t* vflag) {
+__device__ void batch_big(const Ctx& c, BlockShared<W>& sh, const BigWS& wide, uint32_t* big, uint8_t* vflag) {
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < 32) {
     for (uint32_t k = 0; k < sh.nbig; ++k) {
@@ -204,7 +203,7 @@ __device__ void batch_big(Ctx& c, BlockShared<W>& sh, const BigWS& wide, uint32_
         if (lane == 0) raise_error(c.st, kErrWalk, p);
         break;
       }
-      unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+      unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), 0u, p);
       int nc = 0, nb = 0;
       int r = cavity_warp(c, wide.cav, t, p, FP, prio, &nc, &nb);
       if (r == kCandLocated)
@@ -233,8 +232,8 @@ __device__ void batch_big(Ctx& c, BlockShared<W>& sh, const BigWS& wide, uint32_
   __syncthreads();
 }
 
-template <int W>
-__global__ void __launch_bounds__(W * 32) k_batch(Ctx c0, BatchArgs a) {
+template <int W, int MINB>
+__global__ void __launch_bounds__(W * 32, MINB) k_batch(Ctx c0, BatchArgs a) {
   __shared__ BlockShared<W> sh;
   const int tid = threadIdx.x, wid = tid >> 5;
   BigWS ws, wide;
@@ -474,39 +473,55 @@ uint32_t batch_hint_fine() { return kBatchFine; }
 uint32_t batch_hint_coarse() { return kBatchCoarse; }
 int batch_cb() { return kBatchCb; }
 
-int batch_shapes(int* warps, int max_n) {
-  static const int kShapes[] = {4, 8, 16, 32};
+// Block shapes the batch kernel is built for: warps per block and the minimum resident blocks
+// per SM that bounds its registers (128 registers at 8 warps x 2 blocks, 64 at 32 x 1, 32 at
+// 32 x 2). The 32-register shapes spill, but 64 resident warps per SM hide the latency of the
+// pointer chasing better than fewer warps without spills, so the autotuner tries both kinds.
+// A shape is encoded as warps | (min_blocks << 8).
+static const int kShapes[] = {8 | (2 << 8),  8 | (4 << 8),  8 | (8 << 8),  16 | (2 << 8),
+                              16 | (4 << 8), 32 | (1 << 8), 32 | (2 << 8)};
+
+int batch_shapes(int* shapes, int max_n) {
   int n = 0;
-  for (int w : kShapes)
-    if (n < max_n) warps[n++] = w;
+  for (int s : kShapes)
+    if (n < max_n) shapes[n++] = s;
   return n;
 }
 
-// Resident blocks per SM of the batch kernel with W warps (for sizing its workspaces).
-int batch_blocks_per_sm(int W) {
+template <int W, int MINB>
+static int occupancy() {
   int nb = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (W) {
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<4>, 4 * 32, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<8>, 8 * 32, 0); break;
-    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<16>, 16 * 32, 0); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<32>, 32 * 32, 0); break;
-    default: break;
-  }
-  return e == cudaSuccess ? nb : 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<W, MINB>, W * 32, 0) == cudaSuccess ? nb : 0;
 }
 
-int batch_launch(int W, unsigned blocks, const Ctx& c, BatchCloud* clouds, const uint32_t* order, uint32_t n_clouds,
+// Resident blocks per SM of the batch kernel with the given shape (for sizing its workspaces).
+int batch_blocks_per_sm(int shape) {
+  switch (shape) {
+    case 8 | (2 << 8): return occupancy<8, 2>();
+    case 8 | (4 << 8): return occupancy<8, 4>();
+    case 8 | (8 << 8): return occupancy<8, 8>();
+    case 16 | (2 << 8): return occupancy<16, 2>();
+    case 16 | (4 << 8): return occupancy<16, 4>();
+    case 32 | (1 << 8): return occupancy<32, 1>();
+    case 32 | (2 << 8): return occupancy<32, 2>();
+    default: return 0;
+  }
+}
+
+int batch_launch(int shape, unsigned blocks, const Ctx& c, BatchCloud* clouds, const uint32_t* order, uint32_t n_clouds,
                  unsigned int* next, uint8_t* vflag, uint32_t* list_a, uint32_t* list_b, uint32_t* list_big,
                  uint32_t* hint_fine, uint32_t* hint_coarse, DevState* states, char* wsmem, size_t wsstride,
                  float alpha, double gamma, const float* eta, unsigned long long* stats, cudaStream_t s) {
   BatchArgs a{clouds, order, n_clouds, next, vflag, list_a, list_b, list_big, hint_fine, hint_coarse, states,
               wsmem, wsstride, alpha, gamma, eta, stats};
-  switch (W) {
-    case 4: k_batch<4><<<blocks, 4 * 32, 0, s>>>(c, a); break;
-    case 8: k_batch<8><<<blocks, 8 * 32, 0, s>>>(c, a); break;
-    case 16: k_batch<16><<<blocks, 16 * 32, 0, s>>>(c, a); break;
-    case 32: k_batch<32><<<blocks, 32 * 32, 0, s>>>(c, a); break;
+  switch (shape) {
+    case 8 | (2 << 8): k_batch<8, 2><<<blocks, 8 * 32, 0, s>>>(c, a); break;
+    case 8 | (4 << 8): k_batch<8, 4><<<blocks, 8 * 32, 0, s>>>(c, a); break;
+    case 8 | (8 << 8): k_batch<8, 8><<<blocks, 8 * 32, 0, s>>>(c, a); break;
+    case 16 | (2 << 8): k_batch<16, 2><<<blocks, 16 * 32, 0, s>>>(c, a); break;
+    case 16 | (4 << 8): k_batch<16, 4><<<blocks, 16 * 32, 0, s>>>(c, a); break;
+    case 32 | (1 << 8): k_batch<32, 1><<<blocks, 32 * 32, 0, s>>>(c, a); break;
+    case 32 | (2 << 8): k_batch<32, 2><<<blocks, 32 * 32, 0, s>>>(c, a); break;
     default: return DT_EINVAL;
   }
   ++g_kernel_launches;

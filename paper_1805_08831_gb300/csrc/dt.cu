@@ -54,6 +54,7 @@ struct RoundIO {
   int lose_q;
   uint32_t* big_out;
   int big_q;
+  const uint8_t* prank;  // per vertex: scheduling rank of its claims (null: 0)
 };
 
 // ------------------------------------------------------------------ kernels of one round
@@ -113,7 +114,7 @@ template <bool kBig>
 __global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
                                                 const uint32_t* __restrict__ cand_t, uint32_t* cand_status,
                                                 uint32_t* cand_nc, uint32_t* cand_nb, uint32_t* scratch,
-                                                char* bigmem, size_t bigstride) {
+                                                char* bigmem, size_t bigstride, const uint8_t* __restrict__ prank) {
   __shared__ uint32_t s_hkey[kBig ? 1 : kWarps][kHash];
   __shared__ uint8_t s_hval[kBig ? 1 : kWarps][kHash];
   __shared__ uint32_t s_c[kBig ? 1 : kWarps][kCMax];
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint
   if (cand_status[cand] != kCandLocated) return;
   uint32_t p = cand_p[cand];
   PtF FP = load_ptf(c.ptf, p);
-  unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+  unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), prank ? prank[p] : 0u, p);
   CavWS w;
   if (kBig) {
     BigWS b;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
                                                 uint32_t* cand_status, const uint32_t* __restrict__ cand_nc,
                                                 const uint32_t* __restrict__ cand_nb,
                                                 const uint32_t* __restrict__ scratch, char* bigmem,
-                                                size_t bigstride) {
+                                                size_t bigstride, InsertLog lg) {
   constexpr int W = kBig ? 1 : kWarps;
   __shared__ uint4 s_nv[W][kFMax];
   __shared__ uint4 s_nn[W][kFMax];
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
     p = cand_p[cand];
   }
   if (status == kCandLocated) {
-    unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+    unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), io.prank ? io.prank[p] : 0u, p);
     int nc = (int)cand_nc[cand], nb = (int)cand_nb[cand];
     const uint32_t* cl;
     const uint32_t* bl;
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
   unsigned int closer = 0;
   if (lane == 0) {
     if (cand < io.R && status != kCandEmpty) {
+      log_outcome(lg, p, status, status == kCandInserted ? (int)cand_nc[cand] : 0);
       atomicAdd(&s_stat[2], 1ull);
       if (status == kCandLost) atomicAdd(&s_stat[1], 1ull);
       if (status == kCandDup) atomicAdd(&s_stat[5], 1ull);
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
 
 // Points whose cavity exceeds even the large-cavity workspaces: inserted one at a time by one
 // warp with the largest workspaces; nothing else runs concurrently.
-__global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
+__global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws, InsertLog lg) {
   const int lane = threadIdx.x & 31;
   for (uint32_t k = 0; k < n; ++k) {
     uint32_t p = list[k];
@@ -290,7 +292,7 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
       if (lane == 0) raise_error(c.st, kErrWalk, p);
       return;
     }
-    unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+    unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), 0u, p);
     int nc = 0, nb = 0;
     int r = cavity_warp(c, ws.cav, t, p, FP, prio, &nc, &nb);
     if (r != kCandLocated) {
@@ -312,6 +314,7 @@ __global__ void k_huge(Ctx c, const uint32_t* list, uint32_t n, BigWS ws) {
       c.st->anchor = s0;
       c.st->n_inserted += 1;
       c.st->n_big += 1;
+      log_outcome(lg, p, kCandInserted, nc);
       c.st->sum_cavity += nc;
       c.st->sum_ball += nb;
     }
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, const uint
                                                                const uint8_t* __restrict__ vflag,
                                                                uint32_t* list_a, uint32_t* list_b,
                                                                uint32_t* huge_out, char* wsmem, size_t wsstride,
-                                                               float alpha, uint32_t max_passes) {
+                                                               float alpha, uint32_t max_passes, InsertLog lg) {
   __shared__ uint32_t s_p[kCtaWarps], s_t[kCtaWarps], s_st[kCtaWarps], s_nc[kCtaWarps], s_nb[kCtaWarps];
   __shared__ unsigned int s_nout, s_R, s_err;
   __shared__ unsigned long long s_L, s_N0;
@@ -419,7 +422,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, const uint
       // cavity: one warp per candidate, in its own workspace
       if (wid < (int)R && s_st[wid] == kCandLocated) {
         uint32_t p = s_p[wid];
-        unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+        unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), 0u, p);
         int nc = 0, nb = 0;
         int r = cavity_warp(c, ws.cav, s_t[wid], p, load_ptf(c.ptf, p), prio, &nc, &nb);
         if (lane == 0) {
@@ -433,7 +436,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, const uint
       // ball: the same warp, from its workspace
       if (wid < (int)R && s_st[wid] == kCandLocated) {
         uint32_t p = s_p[wid];
-        unsigned long long prio = (__ldcg(&c.st->stamp) << 32) | (unsigned long long)(p + 1u);
+        unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), 0u, p);
         int nc = (int)s_nc[wid], nb = (int)s_nb[wid];
         int r = insert_warp(c, ws.ins, p, prio, ws.cav.clist, nc, ws.cav.blist, nb, nb <= kFMax,
                             __ldcg(&c.st->free_avail), __ldcg(&c.st->bump), c.st->capacity);
@@ -457,6 +460,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, const uint
       __syncthreads();
       if (tid < (int)R) {
         uint32_t st = s_st[tid], p = s_p[tid];
+        if (st != kCandEmpty) log_outcome(lg, p, st, (int)s_nc[tid]);
         if (st != kCandEmpty) atomicAdd(&s_stat[2], 1ull);
         if (st == kCandLost) atomicAdd(&s_stat[1], 1ull);
         if (st == kCandLost || st == kCandWalkLimit) out[atomicAdd(&s_nout, 1u)] = p;
@@ -482,7 +486,8 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, const uint
 // order) against the cumulative wave ends; the stable sort by wave keeps the Moore order.
 __global__ void k_wave_keys(uint32_t vbegin, uint64_t m, uint64_t base, uint64_t rank0,
                             const uint32_t* __restrict__ perm, const uint32_t* __restrict__ rank,
-                            const uint32_t* __restrict__ cum, int nwaves, uint64_t* keys, uint32_t* vals) {
+                            const uint32_t* __restrict__ cum, int nwaves, const uint8_t* __restrict__ risky,
+                            uint64_t* keys, uint32_t* vals) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t v = vbegin + (uint32_t)i;
@@ -493,7 +498,8 @@ __global__ void k_wave_keys(uint32_t vbegin, uint64_t m, uint64_t base, uint64_t
       if (r < cum[mid]) hi = mid;
       else lo = mid + 1;
     }
-    keys[i] = (uint64_t)lo;
+    // with the learned schedule, the points expected to lose go after the rest of their wave
+    keys[i] = risky ? 2 * (uint64_t)lo + risky[v] : (uint64_t)lo;
     vals[i] = v;
   }
 }
@@ -605,6 +611,108 @@ __global__ void k_eval_predicates(int kind, const double* pts, const int64_t* id
   }
 }
 
+// ------------------------------------------------------------------ learned scheduler
+// Cell of a point on a 2^g-per-axis grid over the box, rounding each operation separately.
+__device__ __forceinline__ void grid_cell(const Pt& P, const double* bb, int g, int q[3], double u[3]) {
+  const double G = (double)(1 << g);
+  const double c[3] = {P.x, P.y, P.z};
+  for (int k = 0; k < 3; ++k) {
+    double ext = bb[3 + k] - bb[k];
+    double s = ext > 0.0 ? G / ext : 0.0;
+    double f = floor(__dmul_rn(__dsub_rn(c[k], bb[k]), s));
+    f = f < 0.0 ? 0.0 : (f > G - 1.0 ? G - 1.0 : f);
+    q[k] = (int)f;
+    double w = ext > 0.0 ? __ddiv_rn(__dsub_rn(c[k], bb[k]), ext) : 0.5;
+    u[k] = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+  }
+}
+
+// Points per cell of the grid (vertices [vb, vb + n), duplicates excluded).
+__global__ void k_cell_count(const Pt* __restrict__ pts, const uint8_t* __restrict__ dup_of_input,
+                             const uint32_t* __restrict__ perm, uint32_t vb, uint64_t n, const double* __restrict__ bb,
+                             int g, uint32_t* count) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x) {
+    if (dup_of_input[perm[s]]) continue;
+    int q[3];
+    double u[3];
+    grid_cell(pts[vb + s], bb, g, q, u);
+    atomicAdd(&count[((size_t)q[2] << (2 * g)) | ((size_t)q[1] << g) | (size_t)q[0]], 1u);
+  }
+}
+
+// The eight features of every vertex of the call (see dt_get_features), x[s * 8 + k].
+__global__ void k_features(const Pt* __restrict__ pts, uint32_t vb, uint64_t n, const double* __restrict__ bb, int g,
+                           const uint32_t* __restrict__ count, const uint32_t* __restrict__ perm,
+                           const uint64_t* __restrict__ keys, const uint8_t* __restrict__ rounds, float* x) {
+  const int G = 1 << g;
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x) {
+    int q[3];
+    double u[3];
+    grid_cell(pts[vb + s], bb, g, q, u);
+    auto at = [&](int a, int b, int c) { return count[((size_t)c << (2 * g)) | ((size_t)b << g) | (size_t)a]; };
+    const double nc = at(q[0], q[1], q[2]);
+    double sum = 0.0, mx = -1.0, mn = 1e300;
+    int k = 0;
+    for (int d = 0; d < 3; ++d)
+      for (int e = -1; e <= 1; e += 2) {
+        int r[3] = {q[0], q[1], q[2]};
+        r[d] += e;
+        if (r[d] < 0 || r[d] >= G) continue;
+        double v = at(r[0], r[1], r[2]);
+        sum += v;
+        mx = fmax(mx, v);
+        mn = fmin(mn, v);
+        ++k;
+      }
+    const double mean = k ? sum / k : nc;
+    if (!k) mx = mn = nc;
+    const uint32_t i = perm[s];
+    const uint64_t key = keys[i];
+    double f[8];
+    f[0] = log2(1.0 + nc) / 8.0;
+    f[1] = log2(1.0 + mean) / 8.0;
+    f[2] = (log2(1.0 + mx) - log2(1.0 + mn)) / 8.0;
+    f[3] = (nc - mean) / (1.0 + nc + mean);
+    f[4] = (double)((key >> 57) & 63) / 64.0;
+    f[5] = (double)((key >> 51) & 63) / 64.0;
+    f[6] = (double)rounds[i] / 8.0;
+    f[7] = 2.0 * fmin(fmin(fmin(u[0], 1.0 - u[0]), fmin(u[1], 1.0 - u[1])), fmin(u[2], 1.0 - u[2]));
+    for (int j = 0; j < 8; ++j) x[s * 8 + j] = (float)f[j];
+  }
+}
+
+// Labels of the call's vertices from the insertion log.
+__global__ void k_labels(const uint16_t* __restrict__ log_nc, const uint8_t* __restrict__ log_lost, uint32_t vb,
+                         uint64_t n, float* y, uint8_t* valid) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t nc = log_nc[vb + s];
+    if (y) {
+      y[2 * s] = log2f(1.f + (float)nc);
+      y[2 * s + 1] = log_lost[vb + s] ? 1.f : 0.f;
+    }
+    if (valid) valid[s] = nc > 0 ? 1 : 0;
+  }
+}
+
+// From the network's outputs: the points expected to lose a conflict (logit above logit_tau),
+// and every point's claim rank, 255 - 32 log2(1 + predicted |C|) clamped to [0, 255], so that a
+// point expected to have a small cavity wins against one expected to have a large cavity (each
+// large cavity that wins knocks out every small one it overlaps).
+__global__ void k_risky(const float* __restrict__ pred, uint64_t n, uint32_t vb, float logit_tau, uint8_t* risky,
+                        uint8_t* prank) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x) {
+    risky[vb + s] = pred[2 * s + 1] > logit_tau ? 1 : 0;
+    float r = rintf(255.f - 32.f * pred[2 * s]);
+    prank[vb + s] = (uint8_t)(r < 0.f ? 0.f : (r > 255.f ? 255.f : r));
+  }
+}
+
+// Histogram of the 2 x (wave) sub-wave keys of a BRIO round.
+__global__ void k_key_hist(const uint64_t* __restrict__ keys, uint64_t m, uint32_t* hist) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&hist[keys[i]], 1u);
+}
+
 unsigned grid_for(uint64_t n, int threads) {
   uint64_t b = (n + threads - 1) / threads;
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, 152ull * 32));
@@ -709,6 +817,27 @@ struct dt_handle {
   uint64_t bgraph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t bgraph_kernels = 0;              // kernels in the captured graph
   bool bgraph_used = false;                 // the last batch replayed the graph
+  // learned scheduler
+  uint16_t* log_nc = nullptr;               // DT_FLAG_LOG: |C| of each vertex's insertion
+  uint8_t* log_lost = nullptr;              // DT_FLAG_LOG: conflicts each vertex lost
+  uint64_t cap_log = 0;
+  float* model = nullptr;                   // DT_MLP_PARAMS parameters (device)
+  bool model_loaded = false;
+  float* feat = nullptr;                    // features [n, 8] of the call being scheduled
+  float* pred = nullptr;                    // network outputs [n, 2]
+  uint64_t cap_feat = 0;
+  uint32_t* cell_count = nullptr;
+  uint64_t cap_cells = 0;
+  uint8_t* risky = nullptr;                 // per vertex: expected to lose a conflict
+  uint8_t* prank = nullptr;                 // per vertex: claim rank (smaller predicted cavity: higher)
+  uint64_t cap_risky = 0;
+  bool risky_ready = false;
+  bool prank_ready = false;
+  bool use_prank = true, use_defer = false;  // uses of the network's predictions (deferral measured slower)
+  uint32_t* wave_hist = nullptr;            // sub-wave sizes
+  double risky_scale = 0.25;                // concurrency of the expected losers, relative
+  float risky_logit = 0.f;                  // logit threshold (0: probability one half)
+  uint64_t last_base = 0;                   // the last dt_insert call's vertices
 };
 
 namespace {
@@ -753,6 +882,11 @@ Ctx make_ctx(dt_handle* h) {
   c.ntets = (uint32_t)h->cap_tets;
   c.npts = (uint32_t)h->cap_pts;
   return c;
+}
+
+InsertLog make_log(dt_handle* h) {
+  const bool logging = (h->cfg.flags & DT_FLAG_LOG) && h->log_nc;
+  return InsertLog{logging ? h->log_nc : nullptr, logging ? h->log_lost : nullptr};
 }
 
 int sync_state(dt_handle* h) {
@@ -820,6 +954,7 @@ int reserve_rounds(dt_handle* h, uint64_t qcap) {
     carve(h->hugemem, kHugeHash, kHugeC, kHugeF, kHugeEdge, &h->hugews);
   }
   if (!h->wave_cum && cudaMalloc(&h->wave_cum, 256 * 4) != cudaSuccess) return DT_ENOMEM;
+  if (!h->wave_hist && cudaMalloc(&h->wave_hist, 512 * 4) != cudaSuccess) return DT_ENOMEM;
   if (qcap > h->cap_w) {
     cudaFree(h->wlist);
     h->wlist = nullptr;
@@ -837,9 +972,9 @@ int reserve_rounds(dt_handle* h, uint64_t qcap) {
   return DT_OK;
 }
 
-uint32_t choose_segments(dt_handle* h, uint64_t mesh_vertices, uint64_t m) {
+uint32_t choose_segments(dt_handle* h, uint64_t mesh_vertices, uint64_t m, float alpha_scale = 1.f) {
   if (h->cfg.segments) return (uint32_t)std::min<uint64_t>(std::min<uint64_t>(h->cfg.segments, h->Rmax), m);
-  double r = h->alpha * (double)mesh_vertices;
+  double r = h->alpha * alpha_scale * (double)mesh_vertices;
   uint64_t R = (uint64_t)std::max(1.0, r);
   R = std::min<uint64_t>(R, h->Rmax);
   R = std::min<uint64_t>(R, m);
@@ -862,10 +997,10 @@ void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, bool big, uint6
   unsigned blocks = (R + kWarps - 1) / kWarps;
   if (big)
     k_cavity<true><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
-                                           h->scratch, h->bigmem, h->bigstride);
+                                           h->scratch, h->bigmem, h->bigstride, io.prank);
   else
     k_cavity<false><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
-                                            h->scratch, h->bigmem, h->bigstride);
+                                            h->scratch, h->bigmem, h->bigstride, io.prank);
   ++g_kernel_launches;
   if (prof) {
     cudaEventRecord(h->prof_events[6 * j_prof + 3], s);
@@ -873,10 +1008,10 @@ void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, bool big, uint6
   }
   if (big)
     k_insert<true><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
-                                           h->bigmem, h->bigstride);
+                                           h->bigmem, h->bigstride, make_log(h));
   else
     k_insert<false><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb,
-                                            h->scratch, h->bigmem, h->bigstride);
+                                            h->scratch, h->bigmem, h->bigstride, make_log(h));
   ++g_kernel_launches;
   if (prof) cudaEventRecord(h->prof_events[6 * j_prof + 5], s);
   h->stats.n_rounds++;
@@ -906,7 +1041,8 @@ int run_big(dt_handle* h, const Ctx& c) {
     uint32_t R = (uint32_t)std::min<uint64_t>(nbig, kBigR);
     uint64_t L = (nbig + R - 1) / R;
     for (uint64_t j = 0; j < L; ++j) {
-      RoundIO io{h->queue[kQBig], 0, nbig, L, j, R, h->queue[kQBig2], kQBig2, h->queue[kQHuge], kQHuge};
+      RoundIO io{h->queue[kQBig], 0, nbig, L, j, R, h->queue[kQBig2], kQBig2, h->queue[kQHuge], kQHuge,
+                 h->prank_ready ? h->prank : nullptr};
       launch_round(h, c, io, true, 0);
     }
     if ((rc = sync_state(h)) != DT_OK) return rc;
@@ -917,7 +1053,7 @@ int run_big(dt_handle* h, const Ctx& c) {
   if (nhuge) {
     Ctx cc = c;
     cc.coherent = 1;
-    k_huge<<<1, 32, 0, h->stream>>>(cc, h->queue[kQHuge], (uint32_t)nhuge, h->hugews);
+    k_huge<<<1, 32, 0, h->stream>>>(cc, h->queue[kQHuge], (uint32_t)nhuge, h->hugews, make_log(h));
     ++g_kernel_launches;
     int rc = sync_state(h);
     if (rc != DT_OK) return rc;
@@ -927,10 +1063,11 @@ int run_big(dt_handle* h, const Ctx& c) {
 
 // One pass: rounds over q[0..m) (or the vertex range qbase + [0, m)) split into R segments of
 // length L (segment s offers q[s*L + j] in round j), then the large cavities of the pass.
-int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next) {
+int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next,
+             float alpha_scale = 1.f) {
   uint64_t& kind_rounds = reset_next ? h->stats.n_rounds_retry : h->stats.n_rounds_wave;
   uint64_t mesh = h->st_host->n_inserted;
-  uint32_t R = choose_segments(h, mesh, m);
+  uint32_t R = choose_segments(h, mesh, m, alpha_scale);
   uint64_t L = (m + R - 1) / R;
   int rc = reset_next ? set_queue_lengths(h, {kQNext, kQBig, kQHuge}) : set_queue_lengths(h, {kQBig, kQHuge});
   if (rc != DT_OK) return rc;
@@ -943,7 +1080,8 @@ int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint
     }
   }
   for (uint64_t j = 0; j < L; ++j) {
-    RoundIO io{q, qbase, m, L, j, R, h->queue[kQNext], kQNext, h->queue[kQBig], kQBig};
+    RoundIO io{q, qbase, m, L, j, R, h->queue[kQNext], kQNext, h->queue[kQBig], kQBig,
+               h->prank_ready ? h->prank : nullptr};
     launch_round(h, c, io, false, j);
   }
   kind_rounds += L;
@@ -969,7 +1107,8 @@ int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint
 // Waves of one BRIO round (see run_brio_round): fills h->wlist with the round's vertices grouped
 // by wave, Moore order inside each wave, h->wave_cum with the cumulative wave ends, and returns
 // the number of waves.
-int make_waves(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint64_t base, std::vector<uint32_t>& cum) {
+int make_waves(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint64_t base, std::vector<uint32_t>& cum,
+               std::vector<float>* scale = nullptr) {
   cudaStream_t s = h->stream;
   uint64_t m = vend - vbegin;
   cum.clear();
@@ -985,9 +1124,34 @@ int make_waves(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint64_t
   if (cudaMemcpyAsync(h->wave_cum, cum.data(), cum.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return -1;
   uint64_t rank0 = round == 0 ? 0 : brio_round_end(round - 1);
+  // learned schedule: every wave splits into the points expected to win, then those expected to
+  // lose (inserted with less concurrency)
+  const bool split = scale && h->risky_ready;
   k_wave_keys<<<grid_for(m, 256), 256, 0, s>>>(vbegin, m, base, rank0, h->ows.perm, h->ows.rank, h->wave_cum,
-                                                (int)cum.size(), h->ows.k0, h->ows.v0);
+                                                (int)cum.size(), split ? h->risky : nullptr, h->ows.k0, h->ows.v0);
   ++g_kernel_launches;
+  if (split) {
+    const int nk = 2 * (int)cum.size();
+    cudaMemsetAsync(h->wave_hist, 0, nk * 4, s);
+    k_key_hist<<<grid_for(m, 256), 256, 0, s>>>(h->ows.k0, m, h->wave_hist);
+    ++g_kernel_launches;
+    std::vector<uint32_t> hist(nk);
+    cudaMemcpyAsync(hist.data(), h->wave_hist, nk * 4, cudaMemcpyDeviceToHost, s);
+    bool alt = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, m, 16, h->ows.hist, s);
+    cudaMemcpyAsync(h->wlist, alt ? h->ows.v1 : h->ows.v0, m * 4, cudaMemcpyDeviceToDevice, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    cum.clear();
+    scale->clear();
+    uint64_t end = 0;
+    for (int k = 0; k < nk; ++k) {
+      if (hist[k] == 0) continue;
+      end += hist[k];
+      cum.push_back((uint32_t)end);
+      scale->push_back((k & 1) ? (float)h->risky_scale : 1.f);
+    }
+    return (int)cum.size();
+  }
+  if (scale) scale->assign(cum.size(), 1.f);
   bool alt = radix_sort_pairs(h->ows.k0, h->ows.v0, h->ows.k1, h->ows.v1, m, 8, h->ows.hist, s);
   cudaMemcpyAsync(h->wlist, alt ? h->ows.v1 : h->ows.v0, m * 4, cudaMemcpyDeviceToDevice, s);
   return (int)cum.size();
@@ -1006,7 +1170,7 @@ int run_cta_round(dt_handle* h, uint32_t vbegin, uint32_t vend, uint64_t base) {
   cudaEventRecord(h->ev[3], h->stream);
   k_cta_insert<<<1, kCtaWarps * 32, 0, h->stream>>>(cc, h->wlist, h->wave_cum, nw, h->vflag, h->queue[kQNext],
                                                      h->queue[kQBig2], h->queue[kQHuge], h->ctamem, h->ctastride,
-                                                     (float)h->alpha_cta, 1u << 16);
+                                                     (float)h->alpha_cta, 1u << 16, make_log(h));
   ++g_kernel_launches;
   cudaEventRecord(h->ev[4], h->stream);
   h->stats.n_passes++;
@@ -1028,13 +1192,14 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint
   uint64_t m = vend - vbegin;
   uint32_t max_rounds = h->cfg.max_rounds ? h->cfg.max_rounds : (1u << 22);
   std::vector<uint32_t> cum;
-  if (make_waves(h, vbegin, vend, round, base, cum) < 0) return DT_ECUDA;
+  std::vector<float> scale;
+  if (make_waves(h, vbegin, vend, round, base, cum, &scale) < 0) return DT_ECUDA;
   int rc = set_queue_lengths(h, {kQNext});
   if (rc != DT_OK) return rc;
   uint64_t off = 0;
-  for (uint32_t e : cum) {
-    if ((rc = run_pass(h, c, h->wlist + off, 0, e - off, false)) != DT_OK) return rc;
-    off = e;
+  for (size_t w = 0; w < cum.size(); ++w) {
+    if ((rc = run_pass(h, c, h->wlist + off, 0, cum[w] - off, false, scale[w])) != DT_OK) return rc;
+    off = cum[w];
   }
   uint64_t nq = h->st_host->q[kQNext];
   uint32_t pass = 0;
@@ -1069,6 +1234,8 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint
   return DT_OK;
 }
 
+int schedule_learned(dt_handle* h, uint64_t n);
+
 int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
   if (n == 0) return h->has_mesh ? DT_OK : DT_EDEGENERATE;
   if (h->n_pts + n >= 0xFFFFFFF0ull) return DT_EINVAL;
@@ -1084,6 +1251,35 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
   k_build_pts<<<grid_for(n, 256), 256, 0, s>>>(xyz, h->ows.perm, h->ows.dup, n, base, h->pts, h->ptf,
                                                 h->vflag, h->point_hint);
   ++g_kernel_launches;
+  h->last_base = base;
+  h->risky_ready = false;
+  h->prank_ready = false;
+  if (h->cfg.flags & DT_FLAG_LOG) {
+    if (h->cap_pts > h->cap_log) {
+      uint16_t* a = nullptr;
+      uint8_t* b = nullptr;
+      if (cudaMalloc(&a, h->cap_pts * 2) != cudaSuccess || cudaMalloc(&b, h->cap_pts) != cudaSuccess) {
+        cudaFree(a);
+        return DT_ENOMEM;
+      }
+      if (base) {
+        cudaMemcpyAsync(a, h->log_nc, base * 2, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(b, h->log_lost, base, cudaMemcpyDeviceToDevice, s);
+      }
+      cudaStreamSynchronize(s);
+      cudaFree(h->log_nc);
+      cudaFree(h->log_lost);
+      h->log_nc = a;
+      h->log_lost = b;
+      h->cap_log = h->cap_pts;
+    }
+    cudaMemsetAsync(h->log_nc + base, 0, n * 2, s);
+    cudaMemsetAsync(h->log_lost + base, 0, n, s);
+  }
+  if (h->cfg.schedule == DT_SCHED_LEARNED) {
+    if (!h->model_loaded) return DT_ESTATE;
+    if ((rc = schedule_learned(h, n)) != DT_OK) return rc;
+  }
   double bb[6];
   if (cudaMemcpyAsync(bb, h->ows.bbox, 48, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DT_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return DT_ECUDA;
@@ -1196,7 +1392,7 @@ int batch_reserve(dt_handle* h, uint64_t N, uint32_t nc, uint64_t T) {
   for (int i = 0; i < ns; ++i) {
     uint64_t blocks = (uint64_t)std::max(1, batch_blocks_per_sm(shapes[i])) * sms;
     states = std::max(states, blocks);
-    ws = std::max(ws, (size_t)blocks * shapes[i] * batch_ws_stride());
+    ws = std::max(ws, (size_t)blocks * (shapes[i] & 255) * batch_ws_stride());
   }
   if (states > h->cap_bstates) {
     if (!realloc_dev(h->bstates, states)) return DT_ENOMEM;
@@ -1260,17 +1456,13 @@ float batch_run(dt_handle* h, int W, float alpha, const uint32_t* order, uint32_
 // batches with the same signature (cloud count and size range).
 int batch_tune(dt_handle* h, const std::vector<uint32_t>& by_size, uint64_t sig) {
   const uint32_t nc = h->n_clouds;
+  // DT_BATCH_WARPS / DT_BATCH_ALPHA restrict the candidates (warps per block; round size)
   const char* fw = std::getenv("DT_BATCH_WARPS");
   const char* fa = std::getenv("DT_BATCH_ALPHA");
   h->batch_tune_ms = 0.0;
-  if (fw && fa) {
-    h->batch_W = std::atoi(fw);
-    h->batch_alpha = (float)std::atof(fa);
-    h->batch_sig = sig;
-    return DT_OK;
-  }
-  // the sample: every k-th cloud of the size order, enough to fill the GPU a few times
-  const uint32_t want = std::min<uint32_t>(nc, std::max<uint32_t>(4u * (uint32_t)sm_count(), nc / 8));
+  // the sample: every k-th cloud of the size order, a quarter of the batch (at least enough to
+  // fill the GPU several times), so that the trials see the batch's tail as well as its bulk
+  const uint32_t want = std::min<uint32_t>(nc, std::max<uint32_t>(8u * (uint32_t)sm_count(), nc / 4));
   const uint32_t step = std::max<uint32_t>(1, nc / std::max<uint32_t>(want, 1));
   std::vector<uint32_t> sample;
   for (uint32_t k = 0; k < nc && sample.size() < want; k += step) sample.push_back(by_size[k]);
@@ -1278,13 +1470,17 @@ int batch_tune(dt_handle* h, const std::vector<uint32_t>& by_size, uint64_t sig)
     return DT_ECUDA;
   int shapes[8];
   int ns = batch_shapes(shapes, 8);
-  static const float kAlphas[] = {0.1f, 0.3f, 1.0f};
+  if (const char* fs = std::getenv("DT_BATCH_SHAPE")) {  // one exact shape: warps | (min blocks << 8)
+    shapes[0] = std::atoi(fs);
+    ns = 1;
+  }
+  std::vector<float> alphas = {0.1f, 0.3f};
+  if (fa) alphas = {(float)std::atof(fa)};
   float best = -1.f;
   auto t0 = std::chrono::steady_clock::now();
   for (int i = 0; i < ns; ++i) {
-    if (fw && std::atoi(fw) != shapes[i]) continue;
-    for (float a : kAlphas) {
-      if (fa && std::fabs(std::atof(fa) - a) > 1e-6) continue;
+    if (fw && std::atoi(fw) != (shapes[i] & 255)) continue;
+    for (float a : alphas) {
       float ms = batch_run(h, shapes[i], a, h->bsample, (uint32_t)sample.size(), false);
       if (ms < 0.f) return DT_ECUDA;
       if (best < 0.f || ms < best) {
@@ -1348,7 +1544,7 @@ int batch_impl(dt_handle* h, const double* xyz, const uint64_t* off, uint32_t nc
   uint64_t big = off[by_size[0] + 1] - off[by_size[0]];
   uint64_t sig = ((uint64_t)nc << 40) ^ ((uint64_t)(64 - __builtin_clzll(N | 1)) << 32) ^
                  (uint64_t)(64 - __builtin_clzll(big | 1));
-  bool fixed = std::getenv("DT_BATCH_WARPS") && std::getenv("DT_BATCH_ALPHA");
+  const bool fixed = std::getenv("DT_BATCH_WARPS") || std::getenv("DT_BATCH_ALPHA") || std::getenv("DT_BATCH_SHAPE");
   if (fixed || !h->batch_W || h->batch_sig != sig) {
     batch_enqueue_prepare(h, xyz, s);
     cudaMemcpyAsync(&bad, h->ows.bad, 4, cudaMemcpyDeviceToHost, s);
@@ -1442,7 +1638,8 @@ int batch_impl(dt_handle* h, const double* xyz, const uint64_t* off, uint32_t nc
   h->stats.n_rounds = st[8];
   h->stats.n_passes = 0;
   h->stats.n_clouds_degenerate = degenerate;
-  h->stats.batch_warps = (uint64_t)h->batch_W;
+  h->stats.batch_warps = (uint64_t)(h->batch_W & 255);
+  h->stats.batch_min_blocks = (uint64_t)(h->batch_W >> 8);
   h->stats.batch_alpha = h->batch_alpha;
   h->stats.ms_batch_tune = h->batch_tune_ms;
   h->stats.batch_graph = h->bgraph_used ? 1 : 0;
@@ -1526,6 +1723,68 @@ int batch_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_t
   return rc;
 }
 
+
+// ------------------------------------------------------------------ learned scheduler (host)
+// Feature grid bits: about four points per cell, at most 2^24 cells.
+int feature_grid_bits(uint64_t n) {
+  int g = 1;
+  while (g < 8 && (1ull << (3 * (g + 1))) * 4ull <= n) ++g;
+  return g;
+}
+
+// Features of the n vertices of the last call into h->feat (grows the buffers).
+int compute_features(dt_handle* h, uint64_t n) {
+  cudaStream_t s = h->stream;
+  if (n > h->cap_feat) {
+    if (!realloc_dev(h->feat, n * 8) || !realloc_dev(h->pred, n * 2)) return DT_ENOMEM;
+    h->cap_feat = n;
+  }
+  const int g = feature_grid_bits(n);
+  const uint64_t cells = 1ull << (3 * g);
+  if (cells > h->cap_cells) {
+    if (!realloc_dev(h->cell_count, cells)) return DT_ENOMEM;
+    h->cap_cells = cells;
+  }
+  cudaMemsetAsync(h->cell_count, 0, cells * 4, s);
+  const uint32_t vb = (uint32_t)h->last_base;
+  k_cell_count<<<grid_for(n, 256), 256, 0, s>>>(h->pts, h->ows.dup, h->ows.perm, vb, n, h->ows.bbox, g, h->cell_count);
+  k_features<<<grid_for(n, 256), 256, 0, s>>>(h->pts, vb, n, h->ows.bbox, g, h->cell_count, h->ows.perm, h->ows.keys,
+                                              h->ows.rounds, h->feat);
+  g_kernel_launches += 2;
+  return cudaPeekAtLastError() == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
+// Learned schedule of the call: features, the network, and the expected losers' flags.
+int schedule_learned(dt_handle* h, uint64_t n) {
+  int rc = compute_features(h, n);
+  if (rc != DT_OK) return rc;
+  if (h->last_base + n > h->cap_risky) {
+    uint8_t *r = nullptr, *k = nullptr;
+    if (cudaMalloc(&r, h->cap_pts) != cudaSuccess || cudaMalloc(&k, h->cap_pts) != cudaSuccess) {
+      cudaFree(r);
+      return DT_ENOMEM;
+    }
+    if (h->risky && h->last_base) {
+      cudaMemcpyAsync(r, h->risky, h->last_base, cudaMemcpyDeviceToDevice, h->stream);
+      cudaMemcpyAsync(k, h->prank, h->last_base, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->risky);
+  cudaFree(h->prank);
+    cudaFree(h->prank);
+    h->risky = r;
+    h->prank = k;
+    h->cap_risky = h->cap_pts;
+  }
+  if ((rc = mlp_forward(h->model, h->feat, n, h->pred, h->stream)) != DT_OK) return rc;
+  k_risky<<<grid_for(n, 256), 256, 0, h->stream>>>(h->pred, n, (uint32_t)h->last_base,
+                                                    h->use_defer ? h->risky_logit : 1e30f, h->risky, h->prank);
+  ++g_kernel_launches;
+  h->risky_ready = h->use_defer;
+  h->prank_ready = h->use_prank;
+  return cudaPeekAtLastError() == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
 void fill_stats(dt_handle* h, dt_stats* o) {
   *o = h->stats;
   o->n_launches = g_kernel_launches - h->launches0;
@@ -1595,6 +1854,12 @@ int dt_clear(dt_handle* h) {
   unsigned long long s = h->has_mesh ? h->st_host->stamp : 0;
   h->next_stamp = std::max(h->next_stamp, s + 1);
   h->has_mesh = false;
+  if (h->next_stamp > (1ull << 23) && h->claim) {
+    // claim priorities hold the stamp in 24 bits: start over from clear claim words
+    if (cudaMemsetAsync(h->claim, 0, 2 * h->cap_tets * sizeof(unsigned long long), h->stream) != cudaSuccess)
+      return DT_ECUDA;
+    h->next_stamp = 1;
+  }
   if (h->batch_mode) {
     // a batch restarts its claim stamps in every cloud: clear the words before anything else
     if (h->claim && cudaMemsetAsync(h->claim, 0, 2 * h->cap_tets * sizeof(unsigned long long), h->stream) != cudaSuccess)
@@ -1750,8 +2015,57 @@ int dt_get_stats(dt_handle* h, dt_stats* out) {
 }
 
 int dt_load_model(dt_handle* h, const float* params_host, uint32_t n_params) {
-  if (!h || !params_host || n_params != 1410) return DT_EINVAL;
-  return DT_ESTATE;
+  if (!h || !params_host || n_params != (uint32_t)mlp_params()) return DT_EINVAL;
+  if (!h->model && cudaMalloc(&h->model, n_params * sizeof(float)) != cudaSuccess) return DT_ENOMEM;
+  if (cudaMemcpyAsync(h->model, params_host, n_params * sizeof(float), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return DT_ECUDA;
+  if (const char* t = std::getenv("DT_RISK_LOGIT")) h->risky_logit = (float)std::atof(t);
+  if (const char* r = std::getenv("DT_RISK_SCALE")) h->risky_scale = std::atof(r);
+  if (const char* u = std::getenv("DT_LEARN_USE")) {  // "rank", "defer" or "both"
+    h->use_prank = std::strstr(u, "rank") || std::strstr(u, "both");
+    h->use_defer = std::strstr(u, "defer") || std::strstr(u, "both");
+  }
+  h->model_loaded = true;
+  return DT_OK;
+}
+
+int dt_get_features(dt_handle* h, float* x_dev, float* y_dev, uint8_t* valid_dev, uint64_t n) {
+  if (!h || !x_dev || h->batch_mode || !h->has_mesh) return DT_EINVAL;
+  if (n != h->last_n) return DT_EINVAL;
+  if ((y_dev || valid_dev) && !((h->cfg.flags & DT_FLAG_LOG) && h->log_nc)) return DT_ESTATE;
+  cudaStream_t s = h->stream;
+  int rc = compute_features(h, n);
+  if (rc != DT_OK) return rc;
+  cudaMemcpyAsync(x_dev, h->feat, n * 8 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (y_dev || valid_dev) {
+    k_labels<<<grid_for(n, 256), 256, 0, s>>>(h->log_nc, h->log_lost, (uint32_t)h->last_base, n, y_dev, valid_dev);
+    ++g_kernel_launches;
+  }
+  return cudaStreamSynchronize(s) == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
+int dt_mlp_forward(const float* params_dev, const float* x_dev, uint64_t n, float* out_dev, void* stream) {
+  if (!params_dev || (n && (!x_dev || !out_dev))) return DT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = mlp_forward(params_dev, x_dev, n, out_dev, s);
+  if (rc != DT_OK) return rc;
+  return cudaStreamSynchronize(s) == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
+int dt_mlp_grad(const float* params_dev, const float* x_dev, const float* y_dev, uint64_t n, float* grad_dev,
+                float* loss_dev, void* stream) {
+  if (!params_dev || !x_dev || !y_dev || !grad_dev || !loss_dev || n == 0) return DT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = mlp_grad(params_dev, x_dev, y_dev, n, grad_dev, loss_dev, s);
+  if (rc != DT_OK) return rc;
+  return cudaStreamSynchronize(s) == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
+int dt_mlp_train(float* params_dev, const float* x_dev, const float* y_dev, uint64_t n, uint32_t steps,
+                 uint32_t batch, float lr, uint64_t seed, float* losses_host, void* stream) {
+  if (!params_dev || !x_dev || !y_dev || n == 0 || batch == 0 || !(lr > 0.f) || n > 0xFFFFFFFFull) return DT_EINVAL;
+  return mlp_train(params_dev, x_dev, y_dev, n, steps, batch, lr, seed, losses_host, (cudaStream_t)stream);
 }
 
 void dt_destroy(dt_handle* h) {
@@ -1801,6 +2115,14 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->bstats);
   cudaFree(h->bnext);
   cudaFree(h->beta);
+  cudaFree(h->log_nc);
+  cudaFree(h->log_lost);
+  cudaFree(h->model);
+  cudaFree(h->feat);
+  cudaFree(h->pred);
+  cudaFree(h->cell_count);
+  cudaFree(h->risky);
+  cudaFree(h->wave_hist);
   if (h->bexec) cudaGraphExecDestroy(h->bexec);
   if (h->bgraph) cudaGraphDestroy(h->bgraph);
   for (auto& e : h->bev)

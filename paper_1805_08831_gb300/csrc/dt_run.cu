@@ -1,11 +1,14 @@
 // dt_run: command-line driver of the C ABI for profiling (no Python).
-//   dt_run N [steps] [seed]
-// Triangulates N points i.i.d. uniform in the unit cube (SplitMix64 stream, the same recipe as
-// the package's synthetic generator) `steps` times on one handle and prints the tetrahedron
-// count, the device time of each step and the handle's counters.
+//   dt_run N [steps] [seed]            one cloud of N points
+//   dt_run batch C [steps] [seed]      C clouds, sizes round(exp(U[ln 50, ln 50000]))
+// Points are i.i.d. uniform in the unit cube (a SplitMix64 stream, as in the package's synthetic
+// generator). Runs `steps` triangulations on one handle and prints the tetrahedron count, the
+// device time of each step and the handle's counters.
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cmath>
+#include <string>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -20,9 +23,21 @@ static uint64_t mix64(uint64_t z) {
 }
 
 int main(int argc, char** argv) {
-  uint64_t n = argc > 1 ? (uint64_t)std::atof(argv[1]) : 1000000;
-  int steps = argc > 2 ? std::atoi(argv[2]) : 1;
-  uint64_t seed = argc > 3 ? std::strtoull(argv[3], nullptr, 10) : 2;
+  const bool batch = argc > 1 && std::string(argv[1]) == "batch";
+  const int a0 = batch ? 2 : 1;
+  uint64_t n = argc > a0 ? (uint64_t)std::atof(argv[a0]) : 1000000;
+  int steps = argc > a0 + 1 ? std::atoi(argv[a0 + 1]) : 1;
+  uint64_t seed = argc > a0 + 2 ? std::strtoull(argv[a0 + 2], nullptr, 10) : 2;
+  std::vector<uint64_t> off;
+  if (batch) {
+    const uint32_t clouds = (uint32_t)n;
+    off.assign(clouds + 1, 0);
+    for (uint32_t c = 0; c < clouds; ++c) {
+      double u = (double)(mix64((seed << 40) + (c + 1) * 0x9E3779B97F4A7C15ull) >> 11) * (1.0 / 9007199254740992.0);
+      off[c + 1] = off[c] + (uint64_t)std::llround(std::exp(std::log(50.0) + u * (std::log(50000.0) - std::log(50.0))));
+    }
+    n = off[clouds];
+  }
   std::vector<double> xyz(3 * n);
   uint64_t base = seed << 32;
   for (uint64_t i = 0; i < 3 * n; ++i)
@@ -41,7 +56,7 @@ int main(int argc, char** argv) {
   for (int s = 0; s < steps; ++s) {
     dt_clear(h);
     cudaEventRecord(e0);
-    rc = dt_insert(h, d, n);
+    rc = batch ? dt_batch(h, d, off.data(), (uint32_t)(off.size() - 1)) : dt_insert(h, d, n);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float ms = 0;

@@ -60,6 +60,28 @@ struct Ctx {
   uint32_t npts;   // vertex slots allocated
 };
 
+// Claim priority of point p in the current round. Section 3.2 settles conflicts by a total
+// order of the points, and any strict order yields the same triangulation: the round's stamp
+// (so older claims never win), then a scheduling rank (0 unless the learned schedule sets one:
+// points expected to have small cavities first), then the point's index.
+__device__ __forceinline__ unsigned long long claim_prio(unsigned long long stamp, uint32_t rank8, uint32_t p) {
+  return (stamp << 40) | ((unsigned long long)rank8 << 32) | (unsigned long long)(p + 1u);
+}
+
+// Training labels of the learned scheduler (DT_FLAG_LOG), kept out of Ctx so the kernels that
+// do not log carry no extra registers: the cavity of each insertion and the conflicts a point
+// lost on the way.
+struct InsertLog {
+  uint16_t* nc;   // per vertex: |C| of its insertion (null: not logging)
+  uint8_t* lost;  // per vertex: conflicts lost before it (saturating)
+};
+
+__device__ __forceinline__ void log_outcome(const InsertLog& g, uint32_t p, uint32_t status, int nc) {
+  if (!g.nc) return;
+  if (status == kCandInserted) g.nc[p] = (uint16_t)(nc < 65535 ? nc : 65535);
+  else if (status == kCandLost && g.lost[p] < 255) g.lost[p] += 1;
+}
+
 // A tetrahedron record read from the mesh only references allocated vertices and slots; a
 // record that does not raises kErrInternal (the kernels then stop using it) instead of
 // letting a bad id reach memory.

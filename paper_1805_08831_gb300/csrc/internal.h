@@ -130,11 +130,11 @@ size_t batch_ws_stride();       // bytes of one warp's workspace
 uint32_t batch_hint_fine();     // fine hint cells per cloud
 uint32_t batch_hint_coarse();   // coarse hint cells per cloud
 int batch_cb();                 // bits per axis of a cloud's fine hint grid
-int batch_shapes(int* warps, int max_n);  // block shapes (warps) the batch kernel is built for
-int batch_blocks_per_sm(int W);           // resident blocks per SM with W warps
+int batch_shapes(int* shapes, int max_n);  // block shapes: warps | (min blocks per SM << 8)
+int batch_blocks_per_sm(int shape);         // resident blocks per SM of a shape
 constexpr int kBatchStatSlots = 11;      // accumulators batch_launch adds into
 // One persistent launch over the clouds order[0 .. n_clouds) (see batch.cu); *next must be 0.
-int batch_launch(int W, unsigned blocks, const Ctx& c, BatchCloud* clouds, const uint32_t* order, uint32_t n_clouds,
+int batch_launch(int shape, unsigned blocks, const Ctx& c, BatchCloud* clouds, const uint32_t* order, uint32_t n_clouds,
                  unsigned int* next, uint8_t* vflag, uint32_t* list_a, uint32_t* list_b, uint32_t* list_big,
                  uint32_t* hint_fine, uint32_t* hint_coarse, DevState* states, char* wsmem, size_t wsstride,
                  float alpha, double gamma, const float* eta, unsigned long long* stats, cudaStream_t s);
@@ -153,4 +153,12 @@ void batch_collect(const BatchCloud* clouds, uint32_t n_clouds, const Tet* tets,
 // Sort keys of collected tetrahedra: (a, b), (c, d) and the cloud.
 void batch_tet_keys(const uint32_t* tets, uint64_t T, const unsigned long long* out_off, uint32_t n_clouds,
                     uint64_t* khi, uint64_t* klo, uint64_t* kcl, uint32_t* idx, cudaStream_t s);
+// ---------------------------------------------------------------- mlp.cu (learned scheduler)
+int mlp_params();
+int mlp_forward(const float* params, const float* x, uint64_t n, float* out, cudaStream_t s);
+int mlp_grad(const float* params, const float* x, const float* y, uint64_t n, float* grad, float* loss,
+             cudaStream_t s);
+int mlp_train(float* params, const float* x, const float* y, uint64_t n, uint32_t steps, uint32_t batch, float lr,
+              uint64_t seed, float* losses_host, cudaStream_t s);
+
 }  // namespace dtg

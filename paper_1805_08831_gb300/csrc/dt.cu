@@ -698,11 +698,11 @@ __global__ void k_labels(const uint16_t* __restrict__ log_nc, const uint8_t* __r
 // and every point's claim rank, 255 - 32 log2(1 + predicted |C|) clamped to [0, 255], so that a
 // point expected to have a small cavity wins against one expected to have a large cavity (each
 // large cavity that wins knocks out every small one it overlaps).
-__global__ void k_risky(const float* __restrict__ pred, uint64_t n, uint32_t vb, float logit_tau, uint8_t* risky,
-                        uint8_t* prank) {
+__global__ void k_risky(const float* __restrict__ pred, uint64_t n, uint32_t vb, float logit_tau, float rank_scale,
+                        uint8_t* risky, uint8_t* prank) {
   for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x) {
     risky[vb + s] = pred[2 * s + 1] > logit_tau ? 1 : 0;
-    float r = rintf(255.f - 32.f * pred[2 * s]);
+    float r = rintf(255.f - rank_scale * pred[2 * s]);
     prank[vb + s] = (uint8_t)(r < 0.f ? 0.f : (r > 255.f ? 255.f : r));
   }
 }
@@ -837,6 +837,7 @@ struct dt_handle {
   uint32_t* wave_hist = nullptr;            // sub-wave sizes
   double risky_scale = 0.25;                // concurrency of the expected losers, relative
   float risky_logit = 0.f;                  // logit threshold (0: probability one half)
+  float rank_scale = 32.f;                  // claim rank steps per unit of predicted log2(1 + |C|)
   uint64_t last_base = 0;                   // the last dt_insert call's vertices
 };
 
@@ -1778,7 +1779,8 @@ int schedule_learned(dt_handle* h, uint64_t n) {
   }
   if ((rc = mlp_forward(h->model, h->feat, n, h->pred, h->stream)) != DT_OK) return rc;
   k_risky<<<grid_for(n, 256), 256, 0, h->stream>>>(h->pred, n, (uint32_t)h->last_base,
-                                                    h->use_defer ? h->risky_logit : 1e30f, h->risky, h->prank);
+                                                    h->use_defer ? h->risky_logit : 1e30f, h->rank_scale, h->risky,
+                                                    h->prank);
   ++g_kernel_launches;
   h->risky_ready = h->use_defer;
   h->prank_ready = h->use_prank;
@@ -2022,6 +2024,7 @@ int dt_load_model(dt_handle* h, const float* params_host, uint32_t n_params) {
     return DT_ECUDA;
   if (const char* t = std::getenv("DT_RISK_LOGIT")) h->risky_logit = (float)std::atof(t);
   if (const char* r = std::getenv("DT_RISK_SCALE")) h->risky_scale = std::atof(r);
+  if (const char* r = std::getenv("DT_RANK_SCALE")) h->rank_scale = (float)std::atof(r);
   if (const char* u = std::getenv("DT_LEARN_USE")) {  // "rank", "defer" or "both"
     h->use_prank = std::strstr(u, "rank") || std::strstr(u, "both");
     h->use_defer = std::strstr(u, "defer") || std::strstr(u, "both");

@@ -28,6 +28,12 @@ import numpy as np  # noqa: E402
 from paper_1805_08831_gb300 import synth  # noqa: E402
 
 METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, bit-exact"
+# DRAM bytes (read + write) per candidate of k_insert<0>, from one ncu capture of its longest
+# launch at 2e6 uniform points (profiles/k_insert_uniform_2e6.md), and the hash of the kernel
+# sources it was taken on: the traffic is reported only while the sources are unchanged.
+INSERT_TRAFFIC_PER_CANDIDATE = 5177.0
+INSERT_TRAFFIC_SOURCES = "eef31d8fdc5ff0b9"
+KERNEL_SOURCES = ["engine.cuh", "dt.cu", "common.cuh", "predicates.cuh"]
 PAPER_1E7_EPYC = 31.3  # Fig. 9, AMD EPYC 7551, 1e7 uniform points (context)
 SEED = 2
 
@@ -50,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=1e6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and learned comparisons added to the default workload's line")
     return ap.parse_args()
 
 
@@ -120,6 +128,15 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1805_08831_gb300", "csrc", s), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def kernel_bytes(st):
@@ -206,22 +223,105 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def job_throughput(dist, total_ms, tets, steps, device="cuda"):
+    """Whole-job rate of replicas: the tetrahedra of all ranks over the slowest rank's time.
+    Returns (max total ms, all tetrahedra, Mtets/s)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(total_ms), float(tets)], dtype=torch.float64, device=device)
+        tmax, tsum = t.clone(), t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, tets = float(tmax[0]), float(tsum[1])
+    return float(total_ms), float(tets), float(tets) * steps / (float(total_ms) / 1e3) / 1e6
+
+
+def train_scheduler_on_configs(train_steps):
+    """The learned scheduler trained on the GPU on plain-schedule round logs of the uniform (1e5,
+    1e7) and degenerate (1e7) workloads; returns (params, losses, seconds)."""
+    from paper_1805_08831_gb300 import learned
+    t0 = time.perf_counter()
+    params, losses = learned.train_scheduler(
+        [synth.uniform_cube(100000, 1), synth.uniform_cube(10000000, 2), synth.degenerate_mix(10000000, 3)],
+        steps=train_steps)
+    return params, losses, time.perf_counter() - t0
+
+
+def timed_inserts(tri, xd, steps, warmup, stream):
+    """Device ms of `steps` dt_clear + dt_insert steps after `warmup` untimed ones, and the last
+    step's counters and tetrahedron count."""
+    import torch
+    for _ in range(warmup):
+        tri.clear()
+        tri.insert(xd)
+    torch.cuda.synchronize()
+    ms, st = [], None
+    for _ in range(steps):
+        tri.clear()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tri.insert(xd)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        st = tri.stats()
+    return ms, st, tri.num_tets()
+
+
+def learned_vs_plain(n, steps, warmup, train_steps, params=None):
+    """The cube + slab workload (the learned scheduler's target) with the plain and the learned
+    schedule on the same GPU: same tetrahedra, Mtets/s and conflicts of each."""
+    import torch
+    import paper_1805_08831_gb300 as dt
+    info = {}
+    if params is None:
+        params, losses, train_s = train_scheduler_on_configs(train_steps)
+        info.update({"train_s": train_s, "train_steps": train_steps,
+                     "train_loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())]})
+    x = synth.cube_and_slab(int(n), SEED)
+    xd = torch.from_numpy(x).cuda()
+    stream = torch.cuda.current_stream()
+    for name, sched in (("plain", dt.DT_SCHED_PLAIN), ("learned", dt.DT_SCHED_LEARNED)):
+        tri = dt.Triangulation(seed=SEED, stream=stream, schedule=sched)
+        if sched == dt.DT_SCHED_LEARNED:
+            tri.load_model(params)
+        ms, st, T = timed_inserts(tri, xd, steps, warmup, stream)
+        info[name] = {"value": T * len(ms) / (sum(ms) / 1e3) / 1e6, "unit": "Mtets/s",
+                      "ms_per_step": sum(ms) / len(ms), "tets": T, "n_conflicts": st["n_conflicts"],
+                      "n_attempts": st["n_attempts"], "n_rounds": st["n_rounds"], "n_passes": st["n_passes"]}
+        tri.close()
+    info["workload"] = workload_name("slab", n)
+    info["learned_over_plain"] = info["learned"]["value"] / info["plain"]["value"]
+    return info, params
+
+
 def batch_workload_name(n_clouds):
     return (f"{n_clouds} independent clouds, sizes log-uniform in [50, 50000], each i.i.d. uniform "
             f"in its own unit cube, float64, seed 4")
 
 
 def main_batch(args, rank, world, local):
-    """Batched workload: all clouds in one dt_batch call (one persistent graph-replayed launch)
-    against one plain dt_insert launch sequence per cloud on a sample of the clouds."""
     import torch
-    import paper_1805_08831_gb300 as dt
 
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = run_batch(args, rank, world, local, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_batch(args, rank, world, local, dist):
+    """Batched workload: all clouds in one dt_batch call (one persistent graph-replayed launch)
+    against one plain dt_insert launch sequence per cloud on a sample of the clouds."""
+    import torch
+    import paper_1805_08831_gb300 as dt
+
     xyz, off = synth.batched_clouds(args.clouds, 4 + rank)
     xd = torch.from_numpy(xyz).cuda()
     stream = torch.cuda.current_stream()
@@ -252,16 +352,7 @@ def main_batch(args, rank, world, local):
         barrier()
     clocks = clk.summary()
     ntet = tri.num_tets()
-    mine = np.array([sum(step_ms), float(ntet)], dtype=np.float64)
-    if dist is not None:
-        t = torch.tensor(mine, device="cuda")
-        tmax, tsum = t.clone(), t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, all_tets = float(tmax[0]), float(tsum[1])
-    else:
-        total_ms, all_tets = float(mine[0]), float(mine[1])
-    value = all_tets * args.steps / (total_ms / 1e3) / 1e6
+    total_ms, all_tets, value = job_throughput(dist, sum(step_ms), ntet, args.steps)
 
     # the same clouds one dt_insert each (a full launch sequence per cloud), on a sample spread
     # over the size order, weighted back to the whole batch by points
@@ -348,11 +439,8 @@ def main_batch(args, rank, world, local):
         line["cpu_baseline"] = {"value": n_cpu / t_cpu / 1e6, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{used} whole clouds of the batch, serial CPU oracle, "
                                           f"{n_cpu} tetrahedra in {t_cpu:.2f} s"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     tri.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    return line
 
 
 def main():
@@ -381,31 +469,10 @@ def main():
     flags = 0 if args.no_profile else dt.DT_FLAG_PROFILE
     learned_info = None
     if args.schedule == "learned":
-        # the scheduler is trained on the GPU on round logs of the plain schedule (small versions
-        # of the uniform, degenerate and slab workloads), then the same cloud runs both ways
-        from paper_1805_08831_gb300 import learned
-        t0 = time.perf_counter()
-        params, losses = learned.train_scheduler(
-            [synth.uniform_cube(100000, 1), synth.uniform_cube(1000000, 11), synth.degenerate_mix(1000000, 3),
-             synth.cube_and_slab(1000000, 5)], steps=args.train_steps)
-        train_s = time.perf_counter() - t0
+        # trained on the GPU on plain round logs, then the same cloud runs with the plain schedule
+        params, losses, train_s = train_scheduler_on_configs(args.train_steps)
         plain = dt.Triangulation(seed=SEED, stream=stream, flags=flags)
-        for _ in range(max(1, args.warmup)):
-            plain.clear()
-            plain.insert(xd)
-        torch.cuda.synchronize()
-        p_ms, p_st = [], None
-        for _ in range(args.steps):
-            plain.clear()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            plain.insert(xd)
-            e1.record(stream)
-            e1.synchronize()
-            p_ms.append(e0.elapsed_time(e1))
-            p_st = plain.stats()
-        p_tets = plain.num_tets()
+        p_ms, p_st, p_tets = timed_inserts(plain, xd, args.steps, max(1, args.warmup), stream)
         plain.close()
         learned_info = {"train_s": train_s, "train_steps": args.train_steps,
                         "train_loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())],
@@ -455,17 +522,7 @@ def main():
     clocks = clk.summary()
     ntet = tri.num_tets()
     ms = sum(step_ms) / len(step_ms)
-    mine = np.array([sum(step_ms), float(ntet)], dtype=np.float64)
-    if dist is not None:
-        t = torch.tensor(mine, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, all_tets = float(tmax[0]), float(tsum[1])
-    else:
-        total_ms, all_tets = float(mine[0]), float(mine[1])
-    value = all_tets * args.steps / (total_ms / 1e3) / 1e6
+    total_ms, all_tets, value = job_throughput(dist, sum(step_ms), ntet, args.steps)
 
     # end to end through the host entry points: pinned input in, tetrahedra out
     pinned = torch.from_numpy(x_host).pin_memory()
@@ -496,9 +553,17 @@ def main():
         dom = max(times_k, key=lambda k: times_k[k])
         per_step_ms = times_k[dom] / args.steps
         achieved = bytes_k[dom] / (per_step_ms / 1e3) / 1e9
+        traffic = None
+        cand_per_launch = stat_acc["n_attempts"] / max(stat_acc["n_rounds"], 1)
+        if dom == "insert" and kernel_sources_hash() == INSERT_TRAFFIC_SOURCES:
+            # the capture's bytes per candidate, scaled to this workload's mean candidates per round
+            traffic = INSERT_TRAFFIC_PER_CANDIDATE * cand_per_launch
         roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                    "traffic": None, "share_of_step": per_step_ms / ms,
+                    "traffic": traffic, "traffic_how": "ncu dram bytes per candidate of k_insert<0> (2e6 uniform, "
+                    "longest launch) x mean candidates per round of this run",
+                    "alg_bytes_per_launch": bytes_k[dom] / max(totals["n_profiled"] / args.steps, 1),
+                    "share_of_step": per_step_ms / ms,
                     "kernel_ms_per_step": {k: v / args.steps for k, v in times_k.items()},
                     "launches_per_step": totals["n_profiled"] / args.steps,
                     "alg_bytes_per_step": bytes_k[dom]}
@@ -527,6 +592,20 @@ def main():
     if learned_info is not None:
         learned_info["learned_over_plain"] = value / learned_info["plain"]["value"]
         line["learned"] = learned_info
+    if world == 1 and not args.no_extras and args.kind == "uniform" and args.schedule == "plain":
+        # the other rows of the hot path on the same GPU in the same run: the batched form against
+        # one plain launch sequence per cloud, and the learned schedule against the plain one
+        import argparse as _ap
+        bargs = _ap.Namespace(clouds=args.clouds, steps=3, warmup=2, e2e_steps=0, plain_sample=32,
+                              no_cpu_baseline=True)
+        bl = run_batch(bargs, rank, world, local, None)
+        line["batch"] = {"workload": bl["config"]["workload"], "value": bl["value"], "unit": "Mtets/s",
+                         "ms_per_step": bl["ms_per_step"], "tets": bl["config"]["tets"],
+                         "plain_per_cloud": bl["plain_per_cloud"]["value"],
+                         "batched_over_plain": bl["batched_over_plain"], "roofline_frac": bl["roofline"]["frac"],
+                         "shape": [bl["config"]["batch_warps"], bl["config"]["batch_min_blocks"],
+                                   bl["config"]["batch_alpha"]], "graph_replay": bl["config"]["graph_replay"]}
+        line["learned"], _ = learned_vs_plain(1e7, 3, 1, args.train_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(x_host, args.cpu_sample)
     if rank == 0:

@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=1e6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--max-walk", type=int, default=0, help="walk steps per pass (0: the library default)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and learned comparisons added to the default workload's line")
     return ap.parse_args()
@@ -480,7 +481,7 @@ def main():
                                   "ms_per_step": sum(p_ms) / len(p_ms), "n_conflicts": p_st["n_conflicts"],
                                   "n_attempts": p_st["n_attempts"], "n_rounds": p_st["n_rounds"],
                                   "n_passes": p_st["n_passes"]}}
-    tri = dt.Triangulation(seed=SEED, stream=stream, flags=flags,
+    tri = dt.Triangulation(seed=SEED, stream=stream, flags=flags, max_walk_steps=args.max_walk,
                            schedule=dt.DT_SCHED_LEARNED if args.schedule == "learned" else dt.DT_SCHED_PLAIN)
     if args.schedule == "learned":
         tri.load_model(params)

@@ -61,7 +61,7 @@ typedef struct {
   uint64_t seed;              /* BRIO hash and re-partition randomness */
   void* stream;               /* cudaStream_t to run on; NULL = the default stream */
   uint32_t schedule;          /* DT_SCHED_PLAIN or DT_SCHED_LEARNED */
-  uint32_t max_walk_steps;    /* per walk attempt (a longer walk resumes next pass); 0 = 96 */
+  uint32_t max_walk_steps;    /* per walk attempt (a longer walk resumes next pass); 0 = 48 */
   uint32_t max_rounds;        /* insertion rounds per call before DT_ELIMIT; 0 = 1 << 22 */
   uint32_t segments;          /* concurrent insertions per round; 0 = chosen per round */
   uint32_t flags;             /* DT_FLAG_* */

@@ -19,6 +19,7 @@ namespace dtg {
 namespace {
 
 constexpr int kWarps = 8;  // candidates per 256-thread block in the warp-per-point kernels
+constexpr uint32_t kDefaultWalk = 48;          // walk steps per pass (a longer walk resumes next pass)
 constexpr uint64_t kLongWalkBelow = 8192;      // retry lists shorter than this walk up to
 constexpr uint32_t kLongWalkSteps = 1u << 14;  // this many steps per pass
 constexpr uint32_t kScratchStride = kCMax + kFMax;
@@ -770,7 +771,7 @@ struct dt_handle {
   double* bbox_dev = nullptr;
   bool has_mesh = false;
   uint64_t last_n = 0;
-  double alpha = 0.03;   // candidates per round = alpha * mesh vertices
+  double alpha = 0.02;   // candidates per round = alpha * mesh vertices (measured best at 1e7 and 1e8)
   double gamma = 0.3;    // wave size = gamma * mesh vertices
   double alpha_cta = 0.1;  // candidates per round of the one-block engine (at most 16)
   int walk_threads = 64;   // block size of the thread-per-point walk: small blocks spread a round over every SM
@@ -878,7 +879,7 @@ Ctx make_ctx(dt_handle* h) {
   c.cb = h->cb;
   // a walk that has not arrived after this many steps continues in the next pass, from where it
   // stopped, so one long walk does not hold up a whole round
-  c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : 96u;
+  c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kDefaultWalk;
   c.coherent = 0;
   c.ntets = (uint32_t)h->cap_tets;
   c.npts = (uint32_t)h->cap_pts;
@@ -1410,7 +1411,7 @@ int batch_reserve(dt_handle* h, uint64_t N, uint32_t nc, uint64_t T) {
 Ctx batch_ctx(dt_handle* h) {
   Ctx c = make_ctx(h);
   c.coherent = 1;  // a block reads back the tetrahedra it writes
-  c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : 96u;
+  c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kDefaultWalk;
   return c;
 }
 

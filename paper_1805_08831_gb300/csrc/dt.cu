@@ -1191,7 +1191,6 @@ int run_cta_round(dt_handle* h, uint32_t vbegin, uint32_t vend, uint64_t base) {
 int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint64_t base) {
   Ctx c = make_ctx(h);
   cudaStream_t s = h->stream;
-  uint64_t m = vend - vbegin;
   uint32_t max_rounds = h->cfg.max_rounds ? h->cfg.max_rounds : (1u << 22);
   std::vector<uint32_t> cum;
   std::vector<float> scale;

@@ -200,9 +200,193 @@ static __device__ __noinline__ int ex_det3(const Ex2* r0, const Ex2* r1, const E
   return ex_compress(out, n);
 }
 
+// ----------------------------------------------------------------- exact stage on integers
+// When every coordinate of the points of a predicate is an integer multiple of one power of two
+// 2^E with at most 62 significant bits after scaling (lattice, grid and most clustered inputs),
+// the coordinates divided by 2^E are exact 64-bit integers, and both determinants are exact
+// polynomials in them: sums of products of at most five factors, a 3 x 3 minor (< 2^192) times
+// a squared length (< 2^128). They are evaluated in two's-complement arithmetic on 64-bit limbs
+// (4 limbs for orient3d, 6 for insphere) on the integer pipes, which GB300 runs far faster than
+// its FP64 pipe. Subnormal coordinates or exponents spread over more than about 9 bits keep the
+// expansion arithmetic below.
+struct IntCoord {
+  uint64_t mag;  // odd significand (0 for a zero coordinate)
+  int lo;        // exponent of its lowest bit
+  int bits;      // significant bits
+  bool neg;
+};
+
+__device__ __forceinline__ bool int_coord(double x, IntCoord& c) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  c.neg = (b >> 63) != 0;
+  if (ex == 0 && m == 0) {
+    c.mag = 0;
+    c.lo = 0x7FFFFFFF;
+    c.bits = 0;
+    return true;
+  }
+  if (ex == 0 || ex == 0x7FF) return false;  // subnormal, infinite or NaN
+  m |= 1ull << 52;
+  const int tz = __ffsll((long long)m) - 1;
+  c.mag = m >> tz;
+  c.lo = ex - 1075 + tz;
+  c.bits = 64 - __clzll((long long)c.mag);
+  return true;
+}
+
+// The n coordinates as integers of one common power of two (false if one needs > 62 bits).
+__device__ __forceinline__ bool int_scale(const IntCoord* c, int n, long long* X) {
+  int E = 0x7FFFFFFF;
+  for (int i = 0; i < n; ++i) E = min(E, c[i].lo);
+  for (int i = 0; i < n; ++i) {
+    if (c[i].mag == 0) {
+      X[i] = 0;
+      continue;
+    }
+    const int sh = c[i].lo - E;
+    if (sh > 62 || c[i].bits + sh > 62) return false;
+    const long long v = (long long)(c[i].mag << sh);
+    X[i] = c[i].neg ? -v : v;
+  }
+  return true;
+}
+
+// acc (N limbs, two's complement) += m or -= m (m: an nm-limb magnitude).
+template <int N>
+__device__ __forceinline__ void wide_add(uint64_t* acc, const uint64_t* m, int nm, bool sub) {
+  uint64_t c = 0;
+  for (int i = 0; i < N; ++i) {
+    const uint64_t mi = i < nm ? m[i] : 0ull;
+    if (!sub) {
+      const uint64_t s = acc[i] + mi;
+      const uint64_t c1 = s < mi;
+      const uint64_t s2 = s + c;
+      c = c1 | (s2 < c);
+      acc[i] = s2;
+    } else {
+      const uint64_t dd = acc[i] - mi;
+      const uint64_t b1 = acc[i] < mi;
+      const uint64_t d2 = dd - c;
+      c = b1 | (dd < c);
+      acc[i] = d2;
+    }
+  }
+}
+
+// out[0 .. nm] = m[0 .. nm) * v (magnitudes).
+__device__ __forceinline__ void mag_mul1(const uint64_t* m, int nm, uint64_t v, uint64_t* out) {
+  uint64_t carry = 0;
+  for (int i = 0; i < nm; ++i) {
+    uint64_t lo = m[i] * v;
+    uint64_t hi = __umul64hi(m[i], v);
+    lo += carry;
+    hi += (lo < carry);
+    out[i] = lo;
+    carry = hi;
+  }
+  out[nm] = carry;
+}
+
+__device__ __forceinline__ uint64_t mag64(long long x) { return x < 0 ? (uint64_t)(-x) : (uint64_t)x; }
+
+// det[u; v; w] of integer rows into a 4-limb two's-complement accumulator.
+__device__ __forceinline__ void int_det3(const long long* u, const long long* v, const long long* w, uint64_t* acc) {
+  for (int i = 0; i < 4; ++i) acc[i] = 0;
+  const long long t[6][3] = {{u[0], v[1], w[2]}, {u[0], v[2], w[1]}, {u[1], v[0], w[2]},
+                             {u[1], v[2], w[0]}, {u[2], v[0], w[1]}, {u[2], v[1], w[0]}};
+  const bool minus[6] = {false, true, true, false, false, true};
+  for (int k = 0; k < 6; ++k) {
+    const long long a = t[k][0], b = t[k][1], c = t[k][2];
+    if (a == 0 || b == 0 || c == 0) continue;
+    const bool neg = minus[k] ^ (a < 0) ^ (b < 0) ^ (c < 0);
+    const uint64_t ab[2] = {mag64(a) * mag64(b), __umul64hi(mag64(a), mag64(b))};
+    uint64_t abc[3];
+    mag_mul1(ab, 2, mag64(c), abc);
+    wide_add<4>(acc, abc, 3, neg);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ int wide_sign(const uint64_t* acc) {
+  if (acc[N - 1] >> 63) return -1;
+  for (int i = 0; i < N; ++i)
+    if (acc[i]) return 1;
+  return 0;
+}
+
+// Exact orient3d in integers: true (and *s) when the coordinates fit.
+__device__ __forceinline__ bool orient3d_int(const Pt& a, const Pt& b, const Pt& c, const Pt& d, int* s) {
+  const double v[12] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, d.x, d.y, d.z};
+  IntCoord ic[12];
+  for (int i = 0; i < 12; ++i)
+    if (!int_coord(v[i], ic[i])) return false;
+  long long X[12];
+  if (!int_scale(ic, 12, X)) return false;
+  long long r[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) r[i][k] = X[3 * (i + 1) + k] - X[k];
+  uint64_t acc[4];
+  int_det3(r[0], r[1], r[2], acc);
+  *s = wide_sign<4>(acc);
+  return true;
+}
+
+// Exact insphere in integers (the same determinant as insphere below): true when the
+// coordinates fit.
+__device__ __forceinline__ bool insphere_int(const Pt& a, const Pt& b, const Pt& c, const Pt& d, const Pt& e,
+                                             int* s) {
+  const double v[15] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, d.x, d.y, d.z, e.x, e.y, e.z};
+  IntCoord ic[15];
+  for (int i = 0; i < 15; ++i)
+    if (!int_coord(v[i], ic[i])) return false;
+  long long X[15];
+  if (!int_scale(ic, 15, X)) return false;
+  long long D[4][3];
+  uint64_t L[4][2];
+  for (int i = 0; i < 4; ++i) {
+    L[i][0] = L[i][1] = 0;
+    for (int k = 0; k < 3; ++k) {
+      D[i][k] = X[3 * (i + 1) + k] - X[k];
+      const uint64_t m = mag64(D[i][k]);
+      const uint64_t sq[2] = {m * m, __umul64hi(m, m)};
+      wide_add<2>(L[i], sq, 2, false);  // < 3 * 2^126: no carry out of two limbs
+    }
+  }
+  uint64_t acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < 4; ++k) {
+    int r[3], j = 0;
+    for (int i = 0; i < 4; ++i)
+      if (i != k) r[j++] = i;
+    uint64_t M[4];
+    int_det3(D[r[0]], D[r[1]], D[r[2]], M);
+    const int sm = wide_sign<4>(M);
+    if (sm == 0 || (L[k][0] | L[k][1]) == 0) continue;
+    if (sm < 0) {  // magnitude of M
+      for (int i = 0; i < 4; ++i) M[i] = ~M[i];
+      const uint64_t one = 1;
+      wide_add<4>(M, &one, 1, false);
+    }
+    uint64_t p0[5], p1[5], prod[6];
+    mag_mul1(M, 4, L[k][0], p0);
+    mag_mul1(M, 4, L[k][1], p1);
+    for (int i = 0; i < 6; ++i) prod[i] = 0;
+    wide_add<6>(prod, p0, 5, false);
+    wide_add<5>(prod + 1, p1, 5, false);
+    // sign of the term: (-1)^(k+1) times the sign of the minor
+    const bool neg = ((k == 0 || k == 2) ? true : false) ^ (sm < 0);
+    wide_add<6>(acc, prod, 6, neg);
+  }
+  *s = wide_sign<6>(acc);
+  return true;
+}
+
 static __device__ __noinline__ int orient3d_exact(Pt a, Pt b, Pt c, Pt d,
                                            DevState* st) {
   atomicAdd(&st->n_exact, 1ull);
+  int s;
+  if (orient3d_int(a, b, c, d, &s)) return s;
   bool bad = false;
   Ex2 u[3] = {ex_diff(b.x, a.x), ex_diff(b.y, a.y), ex_diff(b.z, a.z)};
   Ex2 v[3] = {ex_diff(c.x, a.x), ex_diff(c.y, a.y), ex_diff(c.z, a.z)};
@@ -216,6 +400,8 @@ static __device__ __noinline__ int orient3d_exact(Pt a, Pt b, Pt c, Pt d,
 static __device__ __noinline__ int insphere_exact(Pt a, Pt b, Pt c, Pt d, Pt e,
                                            DevState* st) {
   atomicAdd(&st->n_exact, 1ull);
+  int s;
+  if (insphere_int(a, b, c, d, e, &s)) return s;
   bool bad = false;
   const Pt q[4] = {b, c, d, e};
   Ex2 D[4][3];

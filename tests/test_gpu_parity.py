@@ -72,6 +72,38 @@ def test_device_predicates_match_oracle():
             assert q[i] == ref_q and q32[i] == ref_q, i
 
 
+def test_exact_stages_on_lattice_tuples():
+    """Lattice coordinates (i / 99, scaled by powers of two, negated, shifted) are exactly
+    co-spherical and coplanar in many tuples: the integer exact stage decides them, and tuples
+    whose exponents spread too far take the expansion arithmetic; both against the oracle."""
+    rng = np.random.default_rng(23)
+    n = 6000
+    p = rng.integers(0, 5, (n, 5, 3)).astype(np.float64) / 99.0
+    scale = 2.0 ** rng.integers(-30, 30, n)
+    p *= scale[:, None, None]
+    flip = rng.random(n) < 0.3
+    p[flip] *= -1.0
+    shift = rng.random(n) < 0.2
+    p[shift] += rng.integers(-3, 3, (shift.sum(), 1, 3)) * scale[shift][:, None, None]
+    far = rng.random(n) < 0.1  # one coordinate 2^40 times larger: the integer stage declines
+    p[far, 0, 0] += 2.0 ** 40 * scale[far]
+    ids = np.stack([rng.permutation(100)[:5] for _ in range(n)]).astype(np.int64)
+    pt = torch.from_numpy(p).cuda()
+    o = dt.eval_predicates(0, pt).cpu().numpy()
+    s = dt.eval_predicates(1, pt).cpu().numpy()
+    q = dt.eval_predicates(2, pt, torch.from_numpy(ids).cuda()).cpu().numpy()
+    zeros = 0
+    for i in range(n):
+        ref_o = oracle.orient3d(*p[i, :4])
+        ref_s = oracle.insphere(*p[i])
+        zeros += ref_s == 0
+        assert o[i] == ref_o, i
+        assert s[i] == ref_s, i
+        if ref_o > 0:
+            assert q[i] == oracle.insphere_sos(p[i], ids[i]), i
+    assert zeros > n // 20  # many tuples are exactly co-spherical
+
+
 def test_fp32_stage_on_nearly_cospherical_tuples():
     """Points a few ulps off a common sphere, at several scales and offsets: the FP32 stage
     must either be right or defer, never return a wrong sign."""

@@ -56,8 +56,9 @@ struct DevState {
   unsigned long long alloc_cursor;   // virtual allocation cursor of this round
   unsigned long long pending;        // slots freed this round (appended after the round)
   unsigned long long free_capacity;  // size of the free-list array
-  unsigned long long q[4];           // queue lengths: 0 next pass, 1 large cavities,
-                                     // 2 large-cavity retries, 3 serial path
+  unsigned long long q[5];           // queue lengths: 0 next pass, 1 large cavities,
+                                     // 2 large-cavity retries, 3 serial path,
+                                     // 4 cavities too large for the shared-memory large rounds
   unsigned int blocks_done;          // blocks of the insert kernel that finished this round
   unsigned int pad1;
   unsigned int error;                // first DevError raised

@@ -29,6 +29,14 @@ constexpr int kQNext = 0;   // lost a conflict or hit the walk limit: next pass
 constexpr int kQBig = 1;    // cavity too large for shared memory: large-cavity rounds
 constexpr int kQBig2 = 2;   // lost a conflict in a large-cavity round: next large-cavity round
 constexpr int kQHuge = 3;   // cavity too large even for the large-cavity workspace: serial path
+constexpr int kQBigG = 4;   // cavity too large for the shared-memory large rounds: global-memory rounds
+
+// Large-cavity rounds, first tier: one warp per candidate with its workspaces in dynamic shared
+// memory (kMedWarps warps per block), for cavities of up to kMedCN tetrahedra and kMedFN
+// boundary facets. Hash probes and list appends then cost shared-memory latency instead of an
+// L2 round trip; larger cavities go on to the global-memory tier.
+constexpr int kMedWarps = 4;
+constexpr uint32_t kMedHash = 1024, kMedCN = 256, kMedFN = 192, kMedEdge = 512;
 
 // Large-cavity rounds: per-candidate workspaces in global memory.
 constexpr uint32_t kBigR = 1024;      // candidates per large-cavity round
@@ -44,6 +52,7 @@ constexpr uint32_t kHugeF = 1u << 15;
 constexpr uint32_t kHugeEdge = 1u << 17;
 
 inline size_t big_stride() { return carve(nullptr, kBigHashN, kBigCN, kBigFN, kBigEdgeN, nullptr); }
+__host__ __device__ inline size_t med_stride() { return carve(nullptr, kMedHash, kMedCN, kMedFN, kMedEdge, nullptr); }
 
 // Where the candidates of a round come from and where the ones it does not insert go.
 struct RoundIO {
@@ -111,36 +120,47 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c, RoundIO io, const uint8_t* 
   }
 }
 
-template <bool kBig>
+// kMode 0: the shared-memory path (8 candidates per block); 1: large cavities with
+// global-memory workspaces; 2: large cavities with dynamic shared-memory workspaces.
+template <int kMode>
 __global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
                                                 const uint32_t* __restrict__ cand_t, uint32_t* cand_status,
                                                 uint32_t* cand_nc, uint32_t* cand_nb, uint32_t* scratch,
                                                 char* bigmem, size_t bigstride, const uint8_t* __restrict__ prank) {
-  __shared__ uint32_t s_hkey[kBig ? 1 : kWarps][kHash];
-  __shared__ uint8_t s_hval[kBig ? 1 : kWarps][kHash];
-  __shared__ uint32_t s_c[kBig ? 1 : kWarps][kCMax];
-  __shared__ uint32_t s_b[kBig ? 1 : kWarps][kFMax];
+  constexpr bool kSmall = kMode == 0;
+  constexpr int kW = kMode == 2 ? kMedWarps : kWarps;
+  __shared__ uint32_t s_hkey[kSmall ? kWarps : 1][kHash];
+  __shared__ uint8_t s_hval[kSmall ? kWarps : 1][kHash];
+  __shared__ uint32_t s_c[kSmall ? kWarps : 1][kCMax];
+  __shared__ uint32_t s_b[kSmall ? kWarps : 1][kFMax];
+  extern __shared__ __align__(16) char s_dyn[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t cand = blockIdx.x * kWarps + wid;
+  uint32_t cand = blockIdx.x * kW + wid;
   if (cand >= R) return;
   if (cand_status[cand] != kCandLocated) return;
   uint32_t p = cand_p[cand];
   PtF FP = load_ptf(c.ptf, p);
   unsigned long long prio = claim_prio(__ldcg(&c.st->stamp), prank ? prank[p] : 0u, p);
   CavWS w;
-  if (kBig) {
+  if (kMode == 1) {
     BigWS b;
     carve(bigmem + (size_t)cand * bigstride, kBigHashN, kBigCN, kBigFN, kBigEdgeN, &b);
+    w = b.cav;
+  } else if (kMode == 2) {
+    BigWS b;
+    carve(s_dyn + (size_t)wid * med_stride(), kMedHash, kMedCN, kMedFN, kMedEdge, &b);
     w = b.cav;
   } else {
     w = CavWS{s_hkey[wid], s_hval[wid], kHash - 1, s_c[wid], kCMax, s_b[wid], kFMax};
   }
   int nc = 0, nb = 0;
   int r = cavity_warp(c, w, cand_t[cand], p, FP, prio, &nc, &nb);
-  if (!kBig && r == kCandLocated) {
-    uint32_t* dst = scratch + (size_t)cand * kScratchStride;
-    for (int i = lane; i < nc; i += 32) dst[i] = s_c[wid][i];
-    for (int i = lane; i < nb; i += 32) dst[kCMax + i] = s_b[wid][i];
+  if (kMode != 1 && r == kCandLocated) {
+    // the lists outlive the block: the ball kernel reads them back
+    const uint32_t cap = kMode == 2 ? kMedCN : kCMax;
+    uint32_t* dst = scratch + (size_t)cand * (kMode == 2 ? kMedCN + kMedFN : kScratchStride);
+    for (int i = lane; i < nc; i += 32) dst[i] = w.clist[i];
+    for (int i = lane; i < nb; i += 32) dst[cap + i] = w.blist[i];
   }
   if (lane == 0) {
     cand_status[cand] = (uint32_t)r;
@@ -152,13 +172,15 @@ __global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint
 // Ball phase: each warp verifies and inserts one candidate independently (no block barrier);
 // the last warp of each block flushes the block's counters, and the last of those closes the
 // round.
-template <bool kBig>
+template <int kMode>
 __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_t* __restrict__ cand_p,
                                                 uint32_t* cand_status, const uint32_t* __restrict__ cand_nc,
                                                 const uint32_t* __restrict__ cand_nb,
                                                 const uint32_t* __restrict__ scratch, char* bigmem,
                                                 size_t bigstride, InsertLog lg) {
-  constexpr int W = kBig ? 1 : kWarps;
+  constexpr int W = kMode == 0 ? kWarps : 1;
+  constexpr int kW = kMode == 2 ? kMedWarps : kWarps;  // candidates per block
+  extern __shared__ __align__(16) char s_dyn[];
   __shared__ uint4 s_nv[W][kFMax];
   __shared__ uint4 s_nn[W][kFMax];
   __shared__ uint32_t s_out[W][kFMax];
@@ -177,7 +199,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
   }
   __syncthreads();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t cand = blockIdx.x * kWarps + wid;
+  uint32_t cand = blockIdx.x * kW + wid;
   uint32_t status = kCandEmpty, p = kNone;
   if (cand < io.R) {
     status = cand_status[cand];
@@ -189,12 +211,18 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
     const uint32_t* cl;
     const uint32_t* bl;
     InsWS w;
-    if (kBig) {
+    if (kMode == 1) {
       BigWS b;
       carve(bigmem + (size_t)cand * bigstride, kBigHashN, kBigCN, kBigFN, kBigEdgeN, &b);
       w = b.ins;
       cl = b.cav.clist;
       bl = b.cav.blist;
+    } else if (kMode == 2) {
+      BigWS b;
+      carve(s_dyn + (size_t)wid * med_stride(), kMedHash, kMedCN, kMedFN, kMedEdge, &b);
+      w = b.ins;
+      cl = scratch + (size_t)cand * (kMedCN + kMedFN);
+      bl = cl + kMedCN;
     } else {
       w = InsWS{s_nv[wid], s_nn[wid], s_out[wid], s_slot[wid], s_ipos[wid], s_vkey[wid], s_tab[wid],
                 nullptr, nullptr, nullptr, nullptr, 0};
@@ -227,7 +255,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
       else if (status == kCandBig) s_bigq[atomicAdd(&s_nbigq, 1u)] = p;
     }
     __threadfence_block();
-    if (atomicAdd(&s_warps_done, 1u) == kWarps - 1) {
+    if (atomicAdd(&s_warps_done, 1u) == kW - 1) {
       // every warp of the block has counted itself: flush the block's queues and counters
       closer = 1;
       unsigned nl = s_nlose, nbq = s_nbigq;
@@ -245,7 +273,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
       if (s_stat[3]) atomicAdd(&c.st->sum_cavity, s_stat[3]);
       if (s_stat[4]) atomicAdd(&c.st->sum_ball, s_stat[4]);
       if (s_stat[5]) atomicAdd(&c.st->n_dups, s_stat[5]);
-      if (kBig && s_stat[0]) atomicAdd(&c.st->n_big, s_stat[0]);
+      if (kMode != 0 && s_stat[0]) atomicAdd(&c.st->n_big, s_stat[0]);
     }
   }
   // the last warp of the last block closes the round
@@ -760,7 +788,8 @@ struct dt_handle {
   uint32_t Rmax = 0;
   uint32_t *cand_p = nullptr, *cand_t = nullptr, *cand_status = nullptr, *cand_nc = nullptr,
            *cand_nb = nullptr, *scratch = nullptr;
-  uint32_t* queue[4] = {nullptr, nullptr, nullptr, nullptr};  // see kQNext .. kQHuge
+  uint32_t* queue[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // see kQNext .. kQBigG
+  uint32_t* medscratch = nullptr;  // cavity lists of the shared-memory large rounds
   uint64_t cap_q = 0;
   char* bigmem = nullptr;   // kBigR large-cavity workspaces
   size_t bigstride = 0;
@@ -775,6 +804,8 @@ struct dt_handle {
   double gamma = 0.3;    // wave size = gamma * mesh vertices
   double alpha_cta = 0.1;  // candidates per round of the one-block engine (at most 16)
   int walk_threads = 64;   // block size of the thread-per-point walk: small blocks spread a round over every SM
+  bool big_smem = true;    // large cavities try the shared-memory workspaces first
+  int big_smem_skip = 0;   // passes left that go straight to the global-memory tier
   uint32_t* wlist = nullptr;
   uint32_t* wave_cum = nullptr;
   uint64_t cap_w = 0;
@@ -949,6 +980,11 @@ int reserve_rounds(dt_handle* h, uint64_t qcap) {
       return DT_ENOMEM;
     h->bigstride = big_stride();
     if (cudaMalloc(&h->bigmem, h->bigstride * kBigR)) return DT_ENOMEM;
+    if (cudaMalloc(&h->medscratch, (size_t)kBigR * (kMedCN + kMedFN) * 4)) return DT_ENOMEM;
+    const int msmem = (int)(kMedWarps * med_stride());
+    if (cudaFuncSetAttribute(k_cavity<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_insert<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, msmem) != cudaSuccess)
+      return DT_ECUDA;
     h->ctastride = cta_stride();
     if (cudaMalloc(&h->ctamem, h->ctastride * kCtaWarps)) return DT_ENOMEM;
     size_t huge = carve(nullptr, kHugeHash, kHugeC, kHugeF, kHugeEdge, nullptr);
@@ -984,8 +1020,10 @@ uint32_t choose_segments(dt_handle* h, uint64_t mesh_vertices, uint64_t m, float
 }
 
 // One concurrent insertion round: walk, cavity + claims, ball (+ closing the round).
-void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, bool big, uint64_t j_prof) {
-  const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0 && !big;
+// mode 0: a round of the shared-memory path; 1: large cavities with global-memory workspaces;
+// 2: large cavities with shared-memory workspaces.
+void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, int mode, uint64_t j_prof) {
+  const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0 && mode == 0;
   cudaStream_t s = h->stream;
   uint32_t R = io.R;
   if (prof) cudaEventRecord(h->prof_events[6 * j_prof], s);
@@ -996,28 +1034,36 @@ void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, bool big, uint6
     cudaEventRecord(h->prof_events[6 * j_prof + 1], s);
     cudaEventRecord(h->prof_events[6 * j_prof + 2], s);
   }
-  unsigned blocks = (R + kWarps - 1) / kWarps;
-  if (big)
-    k_cavity<true><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
-                                           h->scratch, h->bigmem, h->bigstride, io.prank);
+  const unsigned blocks = (R + kWarps - 1) / kWarps;
+  const unsigned mblocks = (R + kMedWarps - 1) / kMedWarps;
+  const size_t msmem = (size_t)kMedWarps * med_stride();
+  if (mode == 1)
+    k_cavity<1><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
+                                        h->scratch, h->bigmem, h->bigstride, io.prank);
+  else if (mode == 2)
+    k_cavity<2><<<mblocks, kMedWarps * 32, msmem, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc,
+                                                         h->cand_nb, h->medscratch, nullptr, 0, io.prank);
   else
-    k_cavity<false><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
-                                            h->scratch, h->bigmem, h->bigstride, io.prank);
+    k_cavity<0><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
+                                        h->scratch, h->bigmem, h->bigstride, io.prank);
   ++g_kernel_launches;
   if (prof) {
     cudaEventRecord(h->prof_events[6 * j_prof + 3], s);
     cudaEventRecord(h->prof_events[6 * j_prof + 4], s);
   }
-  if (big)
-    k_insert<true><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
-                                           h->bigmem, h->bigstride, make_log(h));
+  if (mode == 1)
+    k_insert<1><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
+                                        h->bigmem, h->bigstride, make_log(h));
+  else if (mode == 2)
+    k_insert<2><<<mblocks, kMedWarps * 32, msmem, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb,
+                                                         h->medscratch, nullptr, 0, make_log(h));
   else
-    k_insert<false><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb,
-                                            h->scratch, h->bigmem, h->bigstride, make_log(h));
+    k_insert<0><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
+                                        h->bigmem, h->bigstride, make_log(h));
   ++g_kernel_launches;
   if (prof) cudaEventRecord(h->prof_events[6 * j_prof + 5], s);
   h->stats.n_rounds++;
-  if (big) h->stats.n_rounds_big++;
+  if (mode != 0) h->stats.n_rounds_big++;
 }
 
 int set_queue_lengths(dt_handle* h, std::initializer_list<int> which) {
@@ -1030,26 +1076,46 @@ int set_queue_lengths(dt_handle* h, std::initializer_list<int> which) {
 // Large cavities of a pass: rounds of up to kBigR candidates with global-memory workspaces
 // (losers retry in the next such round), then the serial path for any larger ones.
 int run_big(dt_handle* h, const Ctx& c) {
-  uint64_t nbig = h->st_host->q[kQBig];
-  int guard = 0;
-  while (nbig > 0) {
-    if (++guard > 100000) {
-      h->last_dev_error = 101;  // host-side: large-cavity rounds stopped progressing
-      h->last_dev_info = (unsigned)nbig;
-      return DT_ELIMIT;
+  // tier 1 (shared-memory workspaces): losers retry in the next tier-1 round, cavities that
+  // outgrow the workspace move on to tier 2 (global memory), and from there to the serial path
+  // when most of the recent large cavities outgrew the shared-memory workspaces (degenerate
+  // inputs), skip that tier for a while instead of paying for two tiers
+  const bool smem = h->big_smem && h->big_smem_skip == 0;
+  if (h->big_smem_skip > 0) --h->big_smem_skip;
+  const uint64_t listed = h->st_host->q[kQBig];
+  for (int tier = smem ? 2 : 1; tier >= 1; --tier) {
+    const int in_q = kQBig;
+    const int out_q = tier == 2 ? kQBigG : kQHuge;
+    if (tier == 2) {
+      int rc = set_queue_lengths(h, {kQBigG});
+      if (rc != DT_OK) return rc;
+    } else if (smem) {
+      // the cavities the shared-memory tier could not hold become the global tier's list
+      std::swap(h->queue[kQBig], h->queue[kQBigG]);
+      h->st_host->q[kQBig] = h->st_host->q[kQBigG];
+      if (2 * h->st_host->q[kQBig] > listed) h->big_smem_skip = 8;
     }
-    int rc = set_queue_lengths(h, {kQBig2});
-    if (rc != DT_OK) return rc;
-    uint32_t R = (uint32_t)std::min<uint64_t>(nbig, kBigR);
-    uint64_t L = (nbig + R - 1) / R;
-    for (uint64_t j = 0; j < L; ++j) {
-      RoundIO io{h->queue[kQBig], 0, nbig, L, j, R, h->queue[kQBig2], kQBig2, h->queue[kQHuge], kQHuge,
-                 h->prank_ready ? h->prank : nullptr};
-      launch_round(h, c, io, true, 0);
+    uint64_t nbig = h->st_host->q[in_q];
+    int guard = 0;
+    while (nbig > 0) {
+      if (++guard > 100000) {
+        h->last_dev_error = 101;  // host-side: large-cavity rounds stopped progressing
+        h->last_dev_info = (unsigned)nbig;
+        return DT_ELIMIT;
+      }
+      int rc = set_queue_lengths(h, {kQBig2});
+      if (rc != DT_OK) return rc;
+      uint32_t R = (uint32_t)std::min<uint64_t>(nbig, kBigR);
+      uint64_t L = (nbig + R - 1) / R;
+      for (uint64_t j = 0; j < L; ++j) {
+        RoundIO io{h->queue[kQBig], 0, nbig, L, j, R, h->queue[kQBig2], kQBig2, h->queue[out_q], out_q,
+                   h->prank_ready ? h->prank : nullptr};
+        launch_round(h, c, io, tier == 2 ? 2 : 1, 0);
+      }
+      if ((rc = sync_state(h)) != DT_OK) return rc;
+      nbig = h->st_host->q[kQBig2];
+      std::swap(h->queue[kQBig], h->queue[kQBig2]);
     }
-    if ((rc = sync_state(h)) != DT_OK) return rc;
-    nbig = h->st_host->q[kQBig2];
-    std::swap(h->queue[kQBig], h->queue[kQBig2]);
   }
   uint64_t nhuge = h->st_host->q[kQHuge];
   if (nhuge) {
@@ -1084,7 +1150,7 @@ int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint
   for (uint64_t j = 0; j < L; ++j) {
     RoundIO io{q, qbase, m, L, j, R, h->queue[kQNext], kQNext, h->queue[kQBig], kQBig,
                h->prank_ready ? h->prank : nullptr};
-    launch_round(h, c, io, false, j);
+    launch_round(h, c, io, 0, j);
   }
   kind_rounds += L;
   h->stats.n_passes++;
@@ -1830,6 +1896,7 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (const char* a = std::getenv("DT_ALPHA")) h->alpha = std::atof(a);
   if (const char* g = std::getenv("DT_GAMMA")) h->gamma = std::atof(g);
   if (const char* a = std::getenv("DT_ALPHA_CTA")) h->alpha_cta = std::atof(a);
+  if (const char* b = std::getenv("DT_BIG_SMEM")) h->big_smem = std::atoi(b) != 0;
   if (const char* w = std::getenv("DT_WALK_THREADS")) {
     int v = std::atoi(w);
     if (v == 32 || v == 64 || v == 128 || v == 256) h->walk_threads = v;
@@ -2098,6 +2165,7 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->wlist);
   cudaFree(h->wave_cum);
   cudaFree(h->bigmem);
+  cudaFree(h->medscratch);
   cudaFree(h->hugemem);
   cudaFree(h->ctamem);
   cudaFree(h->bbox_dev);

@@ -18,7 +18,8 @@
 namespace dtg {
 namespace {
 
-constexpr int kWarps = 8;  // candidates per 256-thread block in the warp-per-point kernels
+constexpr int kCavWarps = 4;  // candidates per block of the cavity kernel (4 measured faster than 8)
+constexpr int kInsWarps = 8;  // candidates per block of the ball kernel
 constexpr uint32_t kDefaultWalk = 48;          // walk steps per pass (a longer walk resumes next pass)
 constexpr uint64_t kLongWalkBelow = 8192;      // retry lists shorter than this walk up to
 constexpr uint32_t kLongWalkSteps = 1u << 14;  // this many steps per pass
@@ -123,16 +124,16 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c, RoundIO io, const uint8_t* 
 // kMode 0: the shared-memory path (8 candidates per block); 1: large cavities with
 // global-memory workspaces; 2: large cavities with dynamic shared-memory workspaces.
 template <int kMode>
-__global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
+__global__ void __launch_bounds__((kCavWarps > kMedWarps ? kCavWarps : kMedWarps) * 32, 32 / kCavWarps) k_cavity(Ctx c, uint32_t R, const uint32_t* __restrict__ cand_p,
                                                 const uint32_t* __restrict__ cand_t, uint32_t* cand_status,
                                                 uint32_t* cand_nc, uint32_t* cand_nb, uint32_t* scratch,
                                                 char* bigmem, size_t bigstride, const uint8_t* __restrict__ prank) {
   constexpr bool kSmall = kMode == 0;
-  constexpr int kW = kMode == 2 ? kMedWarps : kWarps;
-  __shared__ uint32_t s_hkey[kSmall ? kWarps : 1][kHash];
-  __shared__ uint8_t s_hval[kSmall ? kWarps : 1][kHash];
-  __shared__ uint32_t s_c[kSmall ? kWarps : 1][kCMax];
-  __shared__ uint32_t s_b[kSmall ? kWarps : 1][kFMax];
+  constexpr int kW = kMode == 2 ? kMedWarps : kCavWarps;
+  __shared__ uint32_t s_hkey[kSmall ? kCavWarps : 1][kHash];
+  __shared__ uint8_t s_hval[kSmall ? kCavWarps : 1][kHash];
+  __shared__ uint32_t s_c[kSmall ? kCavWarps : 1][kCMax];
+  __shared__ uint32_t s_b[kSmall ? kCavWarps : 1][kFMax];
   extern __shared__ __align__(16) char s_dyn[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t cand = blockIdx.x * kW + wid;
@@ -173,13 +174,13 @@ __global__ void __launch_bounds__(256, 4) k_cavity(Ctx c, uint32_t R, const uint
 // the last warp of each block flushes the block's counters, and the last of those closes the
 // round.
 template <int kMode>
-__global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_t* __restrict__ cand_p,
+__global__ void __launch_bounds__((kInsWarps > kMedWarps ? kInsWarps : kMedWarps) * 32) k_insert(Ctx c, RoundIO io, const uint32_t* __restrict__ cand_p,
                                                 uint32_t* cand_status, const uint32_t* __restrict__ cand_nc,
                                                 const uint32_t* __restrict__ cand_nb,
                                                 const uint32_t* __restrict__ scratch, char* bigmem,
                                                 size_t bigstride, InsertLog lg) {
-  constexpr int W = kMode == 0 ? kWarps : 1;
-  constexpr int kW = kMode == 2 ? kMedWarps : kWarps;  // candidates per block
+  constexpr int W = kMode == 0 ? kInsWarps : 1;
+  constexpr int kW = kMode == 2 ? kMedWarps : kInsWarps;  // candidates per block
   extern __shared__ __align__(16) char s_dyn[];
   __shared__ uint4 s_nv[W][kFMax];
   __shared__ uint4 s_nn[W][kFMax];
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(256) k_insert(Ctx c, RoundIO io, const uint32_
   __shared__ uint32_t s_vkey[W][32];
   __shared__ uint16_t s_tab[W][32 * 32];
   __shared__ unsigned int s_warps_done, s_nlose, s_nbigq;
-  __shared__ uint32_t s_lose[kWarps], s_bigq[kWarps];
+  __shared__ uint32_t s_lose[kW], s_bigq[kW];
   __shared__ unsigned long long s_stat[6];  // inserted, conflicts, attempts, cavity, ball, dups
   if (threadIdx.x == 0) {
     s_warps_done = 0;
@@ -1034,17 +1035,18 @@ void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, int mode, uint6
     cudaEventRecord(h->prof_events[6 * j_prof + 1], s);
     cudaEventRecord(h->prof_events[6 * j_prof + 2], s);
   }
-  const unsigned blocks = (R + kWarps - 1) / kWarps;
+  const unsigned cblocks = (R + kCavWarps - 1) / kCavWarps;
+  const unsigned iblocks = (R + kInsWarps - 1) / kInsWarps;
   const unsigned mblocks = (R + kMedWarps - 1) / kMedWarps;
   const size_t msmem = (size_t)kMedWarps * med_stride();
   if (mode == 1)
-    k_cavity<1><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
+    k_cavity<1><<<cblocks, kCavWarps * 32, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
                                         h->scratch, h->bigmem, h->bigstride, io.prank);
   else if (mode == 2)
     k_cavity<2><<<mblocks, kMedWarps * 32, msmem, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc,
                                                          h->cand_nb, h->medscratch, nullptr, 0, io.prank);
   else
-    k_cavity<0><<<blocks, 256, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
+    k_cavity<0><<<cblocks, kCavWarps * 32, 0, s>>>(c, R, h->cand_p, h->cand_t, h->cand_status, h->cand_nc, h->cand_nb,
                                         h->scratch, h->bigmem, h->bigstride, io.prank);
   ++g_kernel_launches;
   if (prof) {
@@ -1052,13 +1054,13 @@ void launch_round(dt_handle* h, const Ctx& c, const RoundIO& io, int mode, uint6
     cudaEventRecord(h->prof_events[6 * j_prof + 4], s);
   }
   if (mode == 1)
-    k_insert<1><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
+    k_insert<1><<<iblocks, kInsWarps * 32, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
                                         h->bigmem, h->bigstride, make_log(h));
   else if (mode == 2)
     k_insert<2><<<mblocks, kMedWarps * 32, msmem, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb,
                                                          h->medscratch, nullptr, 0, make_log(h));
   else
-    k_insert<0><<<blocks, 256, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
+    k_insert<0><<<iblocks, kInsWarps * 32, 0, s>>>(c, io, h->cand_p, h->cand_status, h->cand_nc, h->cand_nb, h->scratch,
                                         h->bigmem, h->bigstride, make_log(h));
   ++g_kernel_launches;
   if (prof) cudaEventRecord(h->prof_events[6 * j_prof + 5], s);

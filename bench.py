@@ -31,8 +31,8 @@ METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, b
 # DRAM bytes (read + write) per candidate of k_insert<0>, from one ncu capture of its longest
 # launch at 2e6 uniform points (profiles/k_insert_uniform_2e6.md), and the hash of the kernel
 # sources it was taken on: the traffic is reported only while the sources are unchanged.
-INSERT_TRAFFIC_PER_CANDIDATE = 5177.0
-INSERT_TRAFFIC_SOURCES = "eef31d8fdc5ff0b9"
+INSERT_TRAFFIC_PER_CANDIDATE = 5352.7
+INSERT_TRAFFIC_SOURCES = "2b5deaacf910d3d0"
 KERNEL_SOURCES = ["engine.cuh", "dt.cu", "common.cuh", "predicates.cuh"]
 PAPER_1E7_EPYC = 31.3  # Fig. 9, AMD EPYC 7551, 1e7 uniform points (context)
 SEED = 2
@@ -170,12 +170,24 @@ def run_oracle(x, seed):
 
 
 def cpu_baseline(x_full, sample):
+    """The oracle on the first `sample` points (timed), and whether the GPU path gives the same
+    canonical tetrahedra on that sample (bit-exact, the parity bar)."""
+    import oracle
     m = int(min(sample, len(x_full)))
     x = np.ascontiguousarray(x_full[:m])
-    ntet, dt_s = run_oracle(x, SEED)
+    t0 = time.perf_counter()
+    ref, _ = oracle.delaunay(x, seed=SEED)
+    dt_s = time.perf_counter() - t0
+    ntet = len(ref)
+    import torch
+    import paper_1805_08831_gb300 as dt
+    with dt.Triangulation(seed=SEED) as tri:
+        tri.insert(torch.from_numpy(x).cuda())
+        got = tri.tets_numpy(canonical=True)
     return {"value": ntet / dt_s / 1e6, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
             "sample": f"first {m} points of the workload, serial CPU oracle (exact predicates), "
-                      f"{ntet} tetrahedra in {dt_s:.2f} s"}
+                      f"{ntet} tetrahedra in {dt_s:.2f} s",
+            "bit_exact_on_sample": bool(got.shape == ref.shape and np.array_equal(got, ref))}
 
 
 def reference_arm(args, rank):
@@ -427,7 +439,10 @@ def run_batch(args, rank, world, local, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on whole clouds of the sample until about 15 s of CPU work
         import oracle
-        t_cpu, n_cpu, used = 0.0, 0, 0
+        tri.clear()
+        tri.batch(xd, off)
+        gpu_tets, coff = tri.tets_batch(canonical=True)
+        t_cpu, n_cpu, used, exact = 0.0, 0, 0, True
         for c in sample[::-1]:
             x = np.ascontiguousarray(xyz[int(off[c]):int(off[c + 1])])
             t0 = time.perf_counter()
@@ -435,11 +450,13 @@ def run_batch(args, rank, world, local, dist):
             t_cpu += time.perf_counter() - t0
             n_cpu += len(tets_c)
             used += 1
+            exact = exact and np.array_equal(gpu_tets[int(coff[c]):int(coff[c + 1])], tets_c)
             if t_cpu > 15.0:
                 break
         line["cpu_baseline"] = {"value": n_cpu / t_cpu / 1e6, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{used} whole clouds of the batch, serial CPU oracle, "
-                                          f"{n_cpu} tetrahedra in {t_cpu:.2f} s"}
+                                          f"{n_cpu} tetrahedra in {t_cpu:.2f} s",
+                                "bit_exact_on_sample": bool(exact)}
     tri.close()
     return line
 
@@ -583,6 +600,9 @@ def main():
                                                       "n_rounds_wave", "n_rounds_retry", "n_rounds_big",
                                                       "ms_first_round")},
                    "mean_C": cfb["C"], "mean_F": cfb["F"],
+                   "exact_per_point": stat_acc["n_exact"] / max(stat_acc["n_unique"], 1),
+                   "perturbed_per_point": stat_acc["n_sos"] / max(stat_acc["n_unique"], 1),
+                   "retry_passes": stat_acc["n_passes"],
                    "ms_sort": stat_acc["ms_sort"], "ms_insert": stat_acc["ms_insert"]},
         "e2e": {"value": e2e_value, "unit": "Mtets/s", "h2d_bytes_per_step": n * 24,
                 "d2h_bytes_per_step": T * 16, "ms": statistics.median(e2e_ms)},

@@ -803,7 +803,7 @@ struct dt_handle {
   uint64_t last_n = 0;
   double alpha = 0.02;   // candidates per round = alpha * mesh vertices (measured best at 1e7 and 1e8)
   double gamma = 0.3;    // wave size = gamma * mesh vertices
-  double alpha_cta = 0.1;  // candidates per round of the one-block engine (at most 16)
+  double alpha_cta = 0.05; // candidates per round of the one-block engine per mesh vertex (at most 32)
   int walk_threads = 64;   // block size of the thread-per-point walk: small blocks spread a round over every SM
   bool big_smem = true;    // large cavities try the shared-memory workspaces first
   int big_smem_skip = 0;   // passes left that go straight to the global-memory tier

@@ -1,0 +1,63 @@
+"""The bench's workload at full size (1e7 uniform points, seed 2, the bench's launch settings),
+checked by what holds at any size: every facet is shared by at most two tetrahedra, the
+triangulation is a topological ball (Euler characteristic 1), and sampled tetrahedra are
+positively oriented with an empty circumsphere against all 1e7 points (the oracle's exact
+predicates decide the points that lie near a sphere)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_08831_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1805_08831_gb300 as dt  # noqa: E402
+
+
+def test_uniform_1e7_is_a_delaunay_ball():
+    n = 10 ** 7
+    x = synth.uniform_cube(n, 2)
+    xd = torch.from_numpy(x).cuda()
+    with dt.Triangulation(seed=2) as t:
+        t.insert(xd)
+        tets = t.tets(canonical=False).long()
+        st = t.stats()
+    T = tets.shape[0]
+    assert st["n_unique"] == n and 6.5 * n < T < 6.9 * n
+    # facets: each shared by at most two tetrahedra; those on one tetrahedron bound the hull
+    s, _ = tets.sort(dim=1)
+    fac = torch.cat([s[:, [1, 2, 3]], s[:, [0, 2, 3]], s[:, [0, 1, 3]], s[:, [0, 1, 2]]]).int()
+    _, fcount = torch.unique(fac, dim=0, return_counts=True)
+    assert int(fcount.max()) <= 2
+    F = fcount.numel()
+    hull_facets = int((fcount == 1).sum())
+    del fac, fcount
+    edges = torch.cat([s[:, [0, 1]], s[:, [0, 2]], s[:, [0, 3]], s[:, [1, 2]], s[:, [1, 3]], s[:, [2, 3]]])
+    E = torch.unique(edges[:, 0] * n + edges[:, 1]).numel()
+    del edges
+    V = torch.unique(s).numel()
+    assert V == n
+    assert V - E + F - T == 1
+    assert hull_facets % 2 == 0  # a closed triangulated sphere has an even number of triangles
+    # sampled tetrahedra: positive orientation and an empty circumsphere
+    rng = np.random.default_rng(5)
+    tet_np = tets[torch.from_numpy(rng.choice(T, 24, replace=False)).cuda()].cpu().numpy()
+    for v in tet_np:
+        a, b, c, d = x[v[0]], x[v[1]], x[v[2]], x[v[3]]
+        assert oracle.orient3d(a, b, c, d) > 0
+        # circumcentre in float64, then every point's power against the sphere
+        A = np.array([b - a, c - a, d - a])
+        rhs = 0.5 * np.array([np.dot(b - a, b - a), np.dot(c - a, c - a), np.dot(d - a, d - a)])
+        ctr = a + np.linalg.solve(A, rhs)
+        r2 = np.dot(ctr - a, ctr - a)
+        pw = ((x - ctr) ** 2).sum(axis=1) - r2
+        close = np.nonzero(pw < 1e-9 * max(r2, 1e-30))[0]
+        for i in close:
+            if i in v:
+                continue
+            # exactly: a point strictly inside the sphere of a positive tetrahedron has insphere < 0
+            assert oracle.insphere(a, b, c, d, x[i]) >= 0, (v, i)

@@ -168,8 +168,11 @@ __device__ void batch_pass(const Ctx& c, BlockShared<W>& sh, const BigWS& ws, co
     __threadfence();
     __syncthreads();
     if (tid == 0) sh.stat[8] += 1;
-    finish_round_block(c);
+    // the last warp closes the round while the first walks the next one: walks do not touch the
+    // allocator or the stamp, and the barrier after the walk orders the close before the claims
+    if (wid == W - 1) finish_round_warp(c);
   }
+  __syncthreads();
 }
 
 // The large cavities of a pass, one at a time by warp 0 with the whole block's workspace (the

@@ -497,7 +497,10 @@ __global__ void __launch_bounds__(kCtaWarps * 32) k_cta_insert(Ctx c, const uint
         else if (st == kCandBig) huge_out[atomicAdd(&c.st->q[kQHuge], 1ull)] = p;
         else if (st == kCandDup) atomicAdd(&c.st->n_dups, 1ull);
       }
-      finish_round_block(c);
+      // the last warp closes the round while the first records this round's outcomes and walks
+      // the next: neither touches the allocator or the stamp, and the barrier after the walk
+      // orders the close before the next claims
+      if (wid == kCtaWarps - 1) finish_round_warp(c);
     }
     __syncthreads();
   }

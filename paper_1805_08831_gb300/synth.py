@@ -110,6 +110,16 @@ def cube_and_slab(n: int, seed: int, slab_frac: float = 0.3, thickness: float = 
     return np.ascontiguousarray(np.concatenate([cube, s], axis=0))
 
 
+
+def box_surface(k: int) -> np.ndarray:
+    """Lattice points (i, j, l) / k of the unit cube's surface, k intervals per edge: the vertices
+    of a boundary mesh of the cube with edge length 1 / k, (k + 1)^3 - (k - 1)^3 points, in
+    (l, j, i) order."""
+    g = np.arange(k + 1, dtype=np.float64) / k
+    z, y, x = np.meshgrid(np.arange(k + 1), np.arange(k + 1), np.arange(k + 1), indexing="ij")
+    on = (x == 0) | (x == k) | (y == 0) | (y == k) | (z == 0) | (z == k)
+    return np.ascontiguousarray(np.c_[g[x[on]], g[y[on]], g[z[on]]])
+
 WORKLOADS = {
     "uniform": uniform_cube,
     "degenerate": degenerate_mix,

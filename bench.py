@@ -33,6 +33,7 @@ METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, b
 # sources it was taken on: the traffic is reported only while the sources are unchanged.
 INSERT_TRAFFIC_PER_CANDIDATE = 5384.3
 INSERT_TRAFFIC_SOURCES = "d0c44b5d033b4ad6"
+REFINE_K = 128  # the refinement workload: the unit cube at size 1/128 from its surface lattice
 KERNEL_SOURCES = ["engine.cuh", "dt.cu", "common.cuh", "predicates.cuh"]
 PAPER_1E7_EPYC = 31.3  # Fig. 9, AMD EPYC 7551, 1e7 uniform points (context)
 SEED = 2
@@ -307,6 +308,39 @@ def learned_vs_plain(n, steps, warmup, train_steps, params=None):
     info["workload"] = workload_name("slab", n)
     info["learned_over_plain"] = info["learned"]["value"] / info["plain"]["value"]
     return info, params
+
+
+def refine_run(k, steps, warmup):
+    """Delaunay refinement of the unit cube (Section 5, Algorithm 2 loop, size 1 / k) from the
+    lattice of its surface with k intervals per edge: device ms of dt_insert of the surface plus
+    dt_refine, and the mesh it leaves. dt_refine reads two counts back per iteration, so the
+    events also hold those host round trips."""
+    import torch
+    import paper_1805_08831_gb300 as dt
+    X = synth.box_surface(k)
+    xd = torch.from_numpy(X).cuda()
+    stream = torch.cuda.current_stream()
+    tri = dt.Triangulation(seed=SEED, stream=stream)
+    ms = []
+    for i in range(warmup + steps):
+        tri.clear()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tri.insert(xd)
+        added, iters = tri.refine(1.0 / k)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    T = tri.num_tets()
+    st = tri.stats()
+    tri.close()
+    t = sum(ms) / len(ms)
+    return {"workload": f"unit cube refined at size 1/{k} from its {len(X)}-point surface lattice",
+            "value": T / (t / 1e3) / 1e6, "unit": "Mtets/s", "ms_per_step": t, "steps": steps,
+            "tets": T, "points": len(X) + added, "added": added, "iterations": iters,
+            "device_error": st["device_error"]}
 
 
 def batch_workload_name(n_clouds):
@@ -627,6 +661,7 @@ def main():
                          "shape": [bl["config"]["batch_warps"], bl["config"]["batch_min_blocks"],
                                    bl["config"]["batch_alpha"]], "graph_replay": bl["config"]["graph_replay"]}
         line["learned"], _ = learned_vs_plain(1e7, 3, 1, args.train_steps)
+        line["refine"] = refine_run(REFINE_K, 3, 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(x_host, args.cpu_sample)
     if rank == 0:

@@ -142,6 +142,38 @@ int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n);
  * each cloud. Each cloud's tetrahedra are those of dt_insert on that cloud alone. */
 int dt_batch(dt_handle* h, const double* xyz_dev, const uint64_t* offsets_host, uint32_t n_clouds);
 
+/* Delaunay refinement of the current triangulation inside an axis-aligned box (Section 5,
+ * Algorithm 2: SamplePoints, FilterPoints, InsertPoints, repeated). The box should be the hull
+ * of the points already inserted (for instance their 8 corners are among them): boundary
+ * recovery is not part of this call. One iteration:
+ *  - sample: each finite tetrahedron with circumradius r, r^2 > (ratio * size)^2, gives a
+ *    candidate at its circumcentre when that lies strictly inside the box. The circumcentre of
+ *    the tetrahedron a, b, c, d (vertices in increasing input index) is computed in float64 with
+ *    every operation rounded on its own: u = b - a, v = c - a, w = d - a,
+ *    o = ((|u|^2 (v x w) + |v|^2 (w x u)) + |w|^2 (u x v)) / (2 u . (v x w)), centre = a + o,
+ *    r^2 = o . o, each dot product summed as (x + y) + z;
+ *  - filter: a candidate at squared distance < (spacing * size)^2 from an existing point is
+ *    dropped; of the rest, one at squared distance < (spacing * size)^2 from a remaining
+ *    candidate of higher priority (larger r^2, then the lexicographically smaller sorted tuple
+ *    of its tetrahedron's input indices) is dropped;
+ *  - insert: the survivors, in increasing order of those tuples, are inserted as by dt_insert
+ *    (their input indices follow the last point given before).
+ * The paper's values are ratio = 1.4 and spacing = 0.7. Stops after an iteration with no
+ * survivor or after max_iters iterations that inserted points. *n_added (may be NULL) receives
+ * the points added, *n_iters (may be NULL) the iterations that inserted points.
+ *  - box_host: 6 float64 (host): lo x, y, z, hi x, y, z, lo < hi on every axis.
+ * DT_EINVAL for a non-positive or non-finite size, ratio or spacing, a bad box, or a box wider
+ * than 2^21 filter cells (spacing * size) per axis; DT_ESTATE without a triangulation or after
+ * dt_batch. Insertion errors are returned as by dt_insert, with the counts reached so far. */
+int dt_refine(dt_handle* h, double size, double ratio, double spacing, const double* box_host, uint32_t max_iters,
+              uint64_t* n_added, uint32_t* n_iters);
+
+/* Coordinates of every point given to the handle (dt_insert calls and dt_refine), by input
+ * index: row i of xyz_dev ([rows, 3] float64, device) receives point i when i < rows. *n_points
+ * (may be NULL) receives the number of points; rows = 0 only queries it. DT_ESTATE after
+ * dt_batch. */
+int dt_get_points(dt_handle* h, double* xyz_dev, uint64_t rows, uint64_t* n_points);
+
 /* Copies the finite tetrahedra of the current triangulation into tets_dev ([cap, 4] uint32,
  * device). canonical != 0 rotates and sorts them (see conventions); 0 writes them positively
  * oriented in an unspecified order. *n_tets receives the count; DT_ETOOSMALL if cap < count.

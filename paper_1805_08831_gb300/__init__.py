@@ -116,6 +116,9 @@ def lib():
         L.dt_mlp_forward.argtypes = [p, p, u64, p, p]
         L.dt_mlp_grad.argtypes = [p, p, p, u64, p, p, p]
         L.dt_mlp_train.argtypes = [p, p, p, u64, u32, u32, ctypes.c_float, u64, p, p]
+        L.dt_refine.argtypes = [p, ctypes.c_double, ctypes.c_double, ctypes.c_double, p, u32,
+                                ctypes.POINTER(u64), ctypes.POINTER(u32)]
+        L.dt_get_points.argtypes = [p, p, u64, ctypes.POINTER(u64)]
         for name in exported_names():
             getattr(L, name)
         _lib = L
@@ -202,6 +205,28 @@ class Triangulation:
             raise ValueError("xyz must be [n, 3]")
         self._check_dev(lib().dt_insert_host(self._h, a.ctypes.data_as(ctypes.c_void_p), a.shape[0]),
                         "dt_insert_host")
+
+    def refine(self, size: float, box=(0.0, 0.0, 0.0, 1.0, 1.0, 1.0), ratio: float = 1.4,
+               spacing: float = 0.7, max_iters: int = 100):
+        """Delaunay refinement inside the box (dt_refine): circumcentres of tetrahedra with
+        r > ratio * size, spaced at least spacing * size from every point, inserted until none
+        is left. Returns (points added, iterations)."""
+        b = (ctypes.c_double * 6)(*[float(v) for v in box])
+        added, iters = ctypes.c_uint64(), ctypes.c_uint32()
+        self._check_dev(lib().dt_refine(self._h, float(size), float(ratio), float(spacing), b, int(max_iters),
+                                        ctypes.byref(added), ctypes.byref(iters)), "dt_refine")
+        return added.value, iters.value
+
+    def points(self):
+        """Every point given to the handle, by input index, as a CUDA float64 tensor [n, 3]."""
+        torch = _torch()
+        n = ctypes.c_uint64()
+        _check(lib().dt_get_points(self._h, None, 0, ctypes.byref(n)), "dt_get_points")
+        out = torch.empty((n.value, 3), dtype=torch.float64, device="cuda")
+        if n.value:
+            _check(lib().dt_get_points(self._h, ctypes.c_void_p(out.data_ptr()), n.value, ctypes.byref(n)),
+                   "dt_get_points")
+        return out
 
     def batch(self, xyz, offsets):
         """Triangulates independent clouds in one call: xyz is a CUDA float64 tensor [N, 3] with

@@ -47,10 +47,11 @@ constexpr uint32_t kBigFN = 1024;     // boundary facets
 constexpr uint32_t kBigEdgeN = 4096;  // edge-hash slots
 
 // Serial path (one point at a time, one warp): the largest workspaces.
-constexpr uint32_t kHugeHash = 1u << 17;
+// The serial path's workspace holds cavities of kHugeC tetrahedra at first and grows with the
+// tetrahedron store, up to kHugeCMax: points inserted into a mesh with an empty interior (the first
+// refinement iterations of a surface) can have cavities of a large share of the mesh.
 constexpr uint32_t kHugeC = 1u << 15;
-constexpr uint32_t kHugeF = 1u << 15;
-constexpr uint32_t kHugeEdge = 1u << 17;
+constexpr uint32_t kHugeCMax = 1u << 20;
 
 inline size_t big_stride() { return carve(nullptr, kBigHashN, kBigCN, kBigFN, kBigEdgeN, nullptr); }
 __host__ __device__ inline size_t med_stride() { return carve(nullptr, kMedHash, kMedCN, kMedFN, kMedEdge, nullptr); }
@@ -771,6 +772,7 @@ struct dt_handle {
   dt_config cfg{};
   cudaStream_t stream = nullptr;
   OrderWS ows;
+  RefineWS rws;  // refinement iterations (dt_refine)
   Pt* pts = nullptr;
   PtF* ptf = nullptr;
   double cmax = 0.0;  // largest |coordinate| so far (sets the FP32 stage's eta)
@@ -798,6 +800,7 @@ struct dt_handle {
   char* bigmem = nullptr;   // kBigR large-cavity workspaces
   size_t bigstride = 0;
   char* hugemem = nullptr;  // the serial path's workspace
+  uint32_t huge_c = 0;      // its cavity capacity (tetrahedra and boundary facets)
   char* ctamem = nullptr;   // the one-block engine's per-warp workspaces
   size_t ctastride = 0;
   BigWS hugews{};
@@ -974,6 +977,24 @@ int reserve_tets(dt_handle* h, uint64_t total_pts) {
   return DT_OK;
 }
 
+// The serial path's workspace: cavities of a quarter of the tetrahedron store, between kHugeC
+// and kHugeCMax tetrahedra (visited-set and edge hashes four times that).
+int reserve_huge(dt_handle* h) {
+  uint64_t want = kHugeC;
+  while (want < kHugeCMax && want < h->cap_tets / 4) want <<= 1;
+  if (h->hugemem && want <= h->huge_c) return DT_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaFree(h->hugemem);
+  h->hugemem = nullptr;
+  h->huge_c = 0;
+  const uint32_t c = (uint32_t)want;
+  size_t bytes = carve(nullptr, 4 * c, c, c, 4 * c, nullptr);
+  if (cudaMalloc(&h->hugemem, bytes)) return DT_ENOMEM;
+  carve(h->hugemem, 4 * c, c, c, 4 * c, &h->hugews);
+  h->huge_c = c;
+  return DT_OK;
+}
+
 int reserve_rounds(dt_handle* h, uint64_t qcap) {
   if (!h->cand_p) {
     h->Rmax = 1u << 19;
@@ -991,9 +1012,6 @@ int reserve_rounds(dt_handle* h, uint64_t qcap) {
       return DT_ECUDA;
     h->ctastride = cta_stride();
     if (cudaMalloc(&h->ctamem, h->ctastride * kCtaWarps)) return DT_ENOMEM;
-    size_t huge = carve(nullptr, kHugeHash, kHugeC, kHugeF, kHugeEdge, nullptr);
-    if (cudaMalloc(&h->hugemem, huge)) return DT_ENOMEM;
-    carve(h->hugemem, kHugeHash, kHugeC, kHugeF, kHugeEdge, &h->hugews);
   }
   if (!h->wave_cum && cudaMalloc(&h->wave_cum, 256 * 4) != cudaSuccess) return DT_ENOMEM;
   if (!h->wave_hist && cudaMalloc(&h->wave_hist, 512 * 4) != cudaSuccess) return DT_ENOMEM;
@@ -1124,11 +1142,13 @@ int run_big(dt_handle* h, const Ctx& c) {
   }
   uint64_t nhuge = h->st_host->q[kQHuge];
   if (nhuge) {
+    int rc = reserve_huge(h);
+    if (rc != DT_OK) return rc;
     Ctx cc = c;
     cc.coherent = 1;
     k_huge<<<1, 32, 0, h->stream>>>(cc, h->queue[kQHuge], (uint32_t)nhuge, h->hugews, make_log(h));
     ++g_kernel_launches;
-    int rc = sync_state(h);
+    rc = sync_state(h);
     if (rc != DT_OK) return rc;
   }
   return DT_OK;
@@ -1957,6 +1977,59 @@ int dt_insert(dt_handle* h, const double* xyz_dev, uint64_t n) {
   return insert_impl(h, xyz_dev, n);
 }
 
+int dt_refine(dt_handle* h, double size, double ratio, double spacing, const double* box_host, uint32_t max_iters,
+              uint64_t* n_added, uint32_t* n_iters) {
+  if (n_added) *n_added = 0;
+  if (n_iters) *n_iters = 0;
+  if (!h || !box_host) return DT_EINVAL;
+  if (!(size > 0.0) || !(ratio > 0.0) || !(spacing > 0.0) || !std::isfinite(size * ratio) ||
+      !std::isfinite(size * spacing))
+    return DT_EINVAL;
+  RefineParams p{};
+  double ext = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    p.lo[k] = box_host[k];
+    p.hi[k] = box_host[3 + k];
+    if (!std::isfinite(p.lo[k]) || !std::isfinite(p.hi[k]) || !(p.lo[k] < p.hi[k])) return DT_EINVAL;
+    ext = std::max(ext, p.hi[k] - p.lo[k]);
+  }
+  if (h->batch_mode || !h->has_mesh) return DT_ESTATE;
+  p.thr_r2 = (ratio * size) * (ratio * size);
+  p.thr_d2 = (spacing * size) * (spacing * size);
+  // filter cells a little wider than spacing * size: a pair closer than that is in neighbouring cells
+  p.inv_cell = 1.0 / (spacing * size * (1.0 + 1e-6));
+  const double g = std::floor(ext * p.inv_cell) + 2.0;
+  if (!(g < (double)(1u << 21))) return DT_EINVAL;
+  p.G = (uint32_t)g;
+  p.bits = 1;
+  while ((1u << p.bits) < p.G) ++p.bits;
+  uint64_t added = 0;
+  uint32_t iters = 0;
+  int rc = DT_OK;
+  while (iters < max_iters) {
+    if ((rc = sync_state(h)) != DT_OK) break;
+    uint64_t m = 0, ns = 0;
+    if ((rc = refine_step(h->rws, h->tets, h->st_host->bump, h->pts, h->n_pts, p, &m, &ns, h->stream)) != DT_OK) break;
+    if (ns == 0) break;
+    if ((rc = insert_impl(h, h->rws.xyz, ns)) != DT_OK) break;
+    added += ns;
+    ++iters;
+  }
+  if (n_added) *n_added = added;
+  if (n_iters) *n_iters = iters;
+  return rc;
+}
+
+int dt_get_points(dt_handle* h, double* xyz_dev, uint64_t rows, uint64_t* n_points) {
+  if (!h || (rows > 0 && !xyz_dev)) return DT_EINVAL;
+  if (h->batch_mode) return DT_ESTATE;
+  if (n_points) *n_points = h->n_pts;
+  if (rows == 0) return DT_OK;
+  int rc = points_out(h->pts, h->n_pts, xyz_dev, rows, h->stream);
+  if (rc != DT_OK) return rc;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
 int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n) {
   if (!h || (n > 0 && !xyz_host)) return DT_EINVAL;
   if (h->batch_mode) return DT_ESTATE;
@@ -2148,6 +2221,7 @@ void dt_destroy(dt_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   order_ws_free(h->ows);
+  refine_ws_free(h->rws);
   cudaFree(h->pts);
   cudaFree(h->ptf);
   cudaFree(h->vflag);

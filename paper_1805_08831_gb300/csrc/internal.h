@@ -154,6 +154,35 @@ void batch_collect(const BatchCloud* clouds, uint32_t n_clouds, const Tet* tets,
 void batch_tet_keys(const uint32_t* tets, uint64_t T, const unsigned long long* out_off, uint32_t n_clouds,
                     uint64_t* khi, uint64_t* klo, uint64_t* kcl, uint32_t* idx, cudaStream_t s);
 // ---------------------------------------------------------------- mlp.cu (learned scheduler)
+// ---------------------------------------------------------------- refinement (refine.cu)
+// Parameters of one refinement iteration (Section 5): thresholds (ratio h)^2 and (spacing h)^2,
+// the box, and the filter grid (cells of 1 / inv_cell >= spacing h, G per axis, bits per axis).
+struct RefineParams {
+  double lo[3], hi[3];
+  double thr_r2, thr_d2, inv_cell;
+  uint32_t G;
+  int bits;
+};
+// Device workspace of the refinement iterations, grown on demand and kept by the handle.
+struct RefineWS {
+  double4_32a* cand = nullptr;  // candidate centre x, y, z and r^2
+  uint4* tup = nullptr;     // sorted input-index tuple of the candidate's tetrahedron
+  uint8_t* ok = nullptr;    // passed the existing-point filter
+  uint32_t* surv = nullptr; // survivors
+  double* xyz = nullptr;    // survivors' coordinates in insertion order [n, 3]
+  uint64_t *k0 = nullptr, *k1 = nullptr;
+  uint32_t *v0 = nullptr, *v1 = nullptr, *hist = nullptr;
+  unsigned long long* count = nullptr;  // candidates, survivors
+  uint64_t cap_cand = 0, cap_xyz = 0, cap_grid = 0, hist_cap = 0;
+};
+void refine_ws_free(RefineWS& w);
+// Samples and filters one iteration on tetrahedron slots [0, nslots) of the points pts[0, npts):
+// *n_cand candidates, *n_new survivors whose coordinates are left in w.xyz in insertion order.
+int refine_step(RefineWS& w, const Tet* tets, uint64_t nslots, const Pt* pts, uint64_t npts, const RefineParams& p,
+                uint64_t* n_cand, uint64_t* n_new, cudaStream_t s);
+// Writes the coordinates of pts[0, npts) to row (input index) of xyz[rows, 3].
+int points_out(const Pt* pts, uint64_t npts, double* xyz, uint64_t rows, cudaStream_t s);
+
 int mlp_params();
 int mlp_forward(const float* params, const float* x, uint64_t n, float* out, cudaStream_t s);
 int mlp_grad(const float* params, const float* x, const float* y, uint64_t n, float* grad, float* loss,

@@ -31,8 +31,8 @@ METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, b
 # DRAM bytes (read + write) per candidate of k_insert<0>, from one ncu capture of its longest
 # launch at 2e6 uniform points (profiles/k_insert_uniform_2e6.md), and the hash of the kernel
 # sources it was taken on: the traffic is reported only while the sources are unchanged.
-INSERT_TRAFFIC_PER_CANDIDATE = 5384.3
-INSERT_TRAFFIC_SOURCES = "d0c44b5d033b4ad6"
+INSERT_TRAFFIC_PER_CANDIDATE = 6547.2
+INSERT_TRAFFIC_SOURCES = "3b8b85bf491cb6cb"
 REFINE_K = 128  # the refinement workload: the unit cube at size 1/128 from its surface lattice
 KERNEL_SOURCES = ["engine.cuh", "dt.cu", "common.cuh", "predicates.cuh"]
 PAPER_1E7_EPYC = 31.3  # Fig. 9, AMD EPYC 7551, 1e7 uniform points (context)

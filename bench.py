@@ -185,10 +185,31 @@ def cpu_baseline(x_full, sample):
     with dt.Triangulation(seed=SEED) as tri:
         tri.insert(torch.from_numpy(x).cuda())
         got = tri.tets_numpy(canonical=True)
-    return {"value": ntet / dt_s / 1e6, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
+    base = {"value": ntet / dt_s / 1e6, "unit": "Mtets/s", "cores": 1, "kind": "oracle",
             "sample": f"first {m} points of the workload, serial CPU oracle (exact predicates), "
                       f"{ntet} tetrahedra in {dt_s:.2f} s",
             "bit_exact_on_sample": bool(got.shape == ref.shape and np.array_equal(got, ref))}
+    return base, cpu_paper_scheme(x, ref)
+
+
+def cpu_paper_scheme(x, ref):
+    """The paper's CPU thread scheme (Sections 3.2 to 3.4: Moore-curve partitions, ownership,
+    re-partitioning, thread halving) on the oracle's predicates, on every host core, timed on the
+    same sample, with its tetrahedra compared to the serial oracle's."""
+    try:
+        from oracle import paper_cpu
+        paper_cpu.build()
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        tets, st = paper_cpu.delaunay(x, cores, seed=SEED)
+        dt_s = time.perf_counter() - t0
+        return {"value": len(tets) / dt_s / 1e6, "unit": "Mtets/s", "cores": cores,
+                "kind": "paper's CPU thread scheme on the oracle's predicates",
+                "sample": f"the same {len(x)} points, {len(tets)} tetrahedra in {dt_s:.2f} s",
+                "bit_exact_vs_oracle": bool(tets.shape == ref.shape and np.array_equal(tets, ref)),
+                "passes": st["passes"], "aborted": st["aborted"], "max_threads": st["max_threads"]}
+    except Exception as e:  # a baseline that fails is reported, not fatal to the GPU line
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def reference_arm(args, rank):
@@ -663,7 +684,7 @@ def main():
         line["learned"], _ = learned_vs_plain(1e7, 3, 1, args.train_steps)
         line["refine"] = refine_run(REFINE_K, 3, 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(x_host, args.cpu_sample)
+        line["cpu_baseline"], line["cpu_paper_scheme"] = cpu_baseline(x_host, args.cpu_sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
     tri.close()

@@ -34,9 +34,12 @@ int g_mut = 0;  // planted mistake for mutation tests (0 = none)
 constexpr uint32_t GHOST = 0xFFFFFFFFu;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
+// Predicate counters of the calling thread (the threaded baseline calls the predicates from
+// several threads; the serial oracle runs on one).
 struct Counters {
   int64_t insphere = 0, exact = 0, sos = 0;
-} g_cnt;
+};
+thread_local Counters g_cnt;
 
 // ------------------------------------------------------------------ big integers
 // Sign-magnitude integers with little-endian 32-bit limbs; schoolbook arithmetic.

@@ -633,8 +633,8 @@ def main():
             traffic = INSERT_TRAFFIC_PER_CANDIDATE * cand_per_launch
         roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                    "traffic": traffic, "traffic_how": "ncu dram bytes per candidate of k_insert<0> (2e6 uniform, "
-                    "longest launch) x mean candidates per round of this run",
+                    "traffic": traffic, "traffic_how": "ncu dram bytes per candidate of k_insert<0> (a large launch at 2e6 "
+                    "uniform) x mean candidates per round of this run",
                     "alg_bytes_per_launch": bytes_k[dom] / max(totals["n_profiled"] / args.steps, 1),
                     "share_of_step": per_step_ms / ms,
                     "kernel_ms_per_step": {k: v / args.steps for k, v in times_k.items()},

@@ -126,8 +126,7 @@ struct Worker {
   uint32_t last = 0;
   std::vector<uint32_t> free_slots;
   uint64_t lo = 0, hi = 0;  // the current chunk of fresh slots
-  int64_t walk = 0, cav = 0, ball = 0, inserted = 0, aborted = 0;
-  bool failed = false;
+  int64_t walk = 0, cav = 0, ball = 0;
   std::vector<uint32_t> C;
   std::vector<std::pair<uint32_t, int>> B;
 

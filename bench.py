@@ -332,7 +332,7 @@ def learned_vs_plain(n, steps, warmup, train_steps, params=None):
 
 
 def refine_run(k, steps, warmup):
-    """Delaunay refinement of the unit cube (Section 5, Algorithm 2 loop, size 1 / k) from the
+    """Delaunay refinement of the unit cube (Section 4, Algorithm 2 loop, size 1 / k) from the
     lattice of its surface with k intervals per edge: device ms of dt_insert of the surface plus
     dt_refine, and the mesh it leaves. dt_refine reads two counts back per iteration, so the
     events also hold those host round trips."""

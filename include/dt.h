@@ -142,7 +142,7 @@ int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n);
  * each cloud. Each cloud's tetrahedra are those of dt_insert on that cloud alone. */
 int dt_batch(dt_handle* h, const double* xyz_dev, const uint64_t* offsets_host, uint32_t n_clouds);
 
-/* Delaunay refinement of the current triangulation inside an axis-aligned box (Section 5,
+/* Delaunay refinement of the current triangulation inside an axis-aligned box (Section 4,
  * Algorithm 2: SamplePoints, FilterPoints, InsertPoints, repeated). The box should be the hull
  * of the points already inserted (for instance their 8 corners are among them): boundary
  * recovery is not part of this call. One iteration:

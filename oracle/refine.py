@@ -1,7 +1,7 @@
 """Oracle of Delaunay refinement inside a box (TEST INFRASTRUCTURE ONLY: used by the tests and
 the benchmark's CPU legs, never by the product path).
 
-Section 5, Algorithm 2, the refinement loop (SamplePoints, FilterPoints, InsertPoints), on a
+Section 4, Algorithm 2, the refinement loop (SamplePoints, FilterPoints, InsertPoints), on a
 convex box whose faces are already covered by the input's hull, so that no boundary recovery is
 needed. Plain float64 numpy plus the serial triangulation of `oracle.delaunay`, which is
 re-run from scratch on the grown point set every iteration (the perturbed Delaunay

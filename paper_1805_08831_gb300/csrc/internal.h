@@ -155,7 +155,7 @@ void batch_tet_keys(const uint32_t* tets, uint64_t T, const unsigned long long* 
                     uint64_t* khi, uint64_t* klo, uint64_t* kcl, uint32_t* idx, cudaStream_t s);
 // ---------------------------------------------------------------- mlp.cu (learned scheduler)
 // ---------------------------------------------------------------- refinement (refine.cu)
-// Parameters of one refinement iteration (Section 5): thresholds (ratio h)^2 and (spacing h)^2,
+// Parameters of one refinement iteration (Section 4): thresholds (ratio h)^2 and (spacing h)^2,
 // the box, and the filter grid (cells of 1 / inv_cell >= spacing h, G per axis, bits per axis).
 struct RefineParams {
   double lo[3], hi[3];

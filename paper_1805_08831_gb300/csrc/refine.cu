@@ -1,4 +1,4 @@
-// Delaunay refinement inside a box (Section 5, Algorithm 2: the loop of SamplePoints,
+// Delaunay refinement inside a box (Section 4, Algorithm 2: the loop of SamplePoints,
 // FilterPoints and InsertPoints), the sampling and filtering half. The insertion is the
 // library's concurrent insertion, called by the host loop in dt.cu with the survivors found here.
 //

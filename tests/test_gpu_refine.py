@@ -1,4 +1,4 @@
-"""dt_refine (Section 5, Algorithm 2 loop on a box) against the refinement oracle: the points it
+"""dt_refine (Section 4, Algorithm 2 loop on a box) against the refinement oracle: the points it
 adds (coordinates and input indices, bit for bit), the iterations, and the tetrahedra of the
 refined mesh (bit for bit), on box surfaces, a cloud with its box corners and a surface whose
 near-flat tetrahedra have rounding-dominated circumcentres; then the loop's properties at a size

@@ -1,6 +1,6 @@
 """Pins of the refinement oracle (oracle/refine.py) against what does not depend on it: closed
 forms of circumcentres, the bisector equations, brute-force filters written out here, and the
-properties the loop must leave behind (Section 5, Algorithm 2). The last test plants mistakes
+properties the loop must leave behind (Section 4, Algorithm 2). The last test plants mistakes
 in the oracle and checks that a pin catches each."""
 import itertools
 

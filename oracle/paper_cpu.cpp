@@ -80,7 +80,6 @@ struct PMesh {
   std::unique_ptr<std::atomic<uint8_t>[]> alive;
   std::unique_ptr<uint64_t[]> stamp;  // touched only by the thread that owns the slot
   std::atomic<uint64_t> bump{0};
-  std::atomic<uint64_t> next_stamp{1};
   // Range of every point (input index) under the current pass's partition, computed on first
   // use in a pass: (pass + 1) << 32 | range.
   std::unique_ptr<std::atomic<uint64_t>[]> tag;
@@ -127,8 +126,17 @@ struct Worker {
   std::vector<uint32_t> free_slots;
   uint64_t lo = 0, hi = 0;  // the current chunk of fresh slots
   int64_t walk = 0, cav = 0, ball = 0;
+  uint64_t stamp_seq = 0;  // visit stamps (me + 1) << 48 | sequence: unique across threads
   std::vector<uint32_t> C;
   std::vector<std::pair<uint32_t, int>> B;
+  struct NewTet {
+    std::array<uint32_t, 4> v;
+    int i;
+    uint32_t out;
+  };
+  std::vector<NewTet> nt;  // reused by every insertion of the thread
+  std::vector<uint32_t> slots;
+  std::vector<std::pair<std::pair<uint32_t, uint32_t>, uint32_t>> inner;
 
   explicit Worker(PMesh& m) : M(m) {}
 
@@ -220,7 +228,7 @@ struct Worker {
     bool ok = true;
     if (!conflict(t, p, &ok) || !ok) return 0;
     // cavity: breadth-first search, every tetrahedron read must be this thread's own
-    const uint64_t st = M.next_stamp.fetch_add(1, std::memory_order_relaxed);
+    const uint64_t st = ((uint64_t)(me + 1) << 48) | ++stamp_seq;
     C.clear();
     B.clear();
     C.push_back(t);
@@ -242,13 +250,7 @@ struct Worker {
       }
     }
     // ball (Section 2.5): one new tetrahedron per boundary facet
-    struct NewTet {
-      std::array<uint32_t, 4> v;
-      int i;
-      uint32_t out;
-    };
-    std::vector<NewTet> nt;
-    nt.reserve(B.size());
+    nt.clear();
     for (auto& b : B) {
       uint32_t r[4];
       M.getv(b.first, r);
@@ -260,8 +262,8 @@ struct Worker {
       M.alive[c].store(0, std::memory_order_relaxed);
       free_slots.push_back(c);
     }
-    std::vector<uint32_t> slots(nt.size());
-    std::vector<std::pair<std::pair<uint32_t, uint32_t>, uint32_t>> inner;
+    slots.resize(nt.size());
+    inner.clear();
     for (size_t k = 0; k < nt.size(); ++k) {
       uint32_t s;
       if (!alloc(&s)) return ORACLE_EINTERNAL;
@@ -296,6 +298,115 @@ struct Worker {
     return 1;
   }
 };
+
+// Runs f(a, b) on [0, n) cut into T contiguous pieces, one thread each.
+template <class F>
+void parallel_for(size_t n, int T, F f) {
+  if (T <= 1 || n < 4096) {
+    f((size_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int w = 1; w < T; ++w) th.emplace_back(f, n * w / T, n * (w + 1) / T);
+  f((size_t)0, n / T);
+  for (auto& x : th) x.join();
+}
+
+// Sorts with T threads: pieces sorted in parallel, then merged pairwise in parallel rounds. The
+// comparators used here are strict total orders (ties broken by index), so the result is the
+// one std::sort gives.
+template <class T_, class Cmp>
+void parallel_sort(std::vector<T_>& v, int T, Cmp cmp) {
+  const size_t n = v.size();
+  if (T <= 1 || n < 65536) {
+    std::sort(v.begin(), v.end(), cmp);
+    return;
+  }
+  std::vector<size_t> b(T + 1);
+  for (int i = 0; i <= T; ++i) b[i] = n * (size_t)i / (size_t)T;
+  {
+    std::vector<std::thread> th;
+    for (int i = 0; i < T; ++i) th.emplace_back([&, i] { std::sort(v.begin() + b[i], v.begin() + b[i + 1], cmp); });
+    for (auto& x : th) x.join();
+  }
+  for (int width = 1; width < T; width *= 2) {
+    std::vector<std::thread> th;
+    for (int i = 0; i + width < T; i += 2 * width) {
+      const size_t lo = b[i], mid = b[i + width], hi = b[std::min(i + 2 * width, T)];
+      th.emplace_back([&, lo, mid, hi] { std::inplace_merge(v.begin() + lo, v.begin() + mid, v.begin() + hi, cmp); });
+    }
+    for (auto& x : th) x.join();
+  }
+}
+
+// The insertion order of the serial oracle (duplicates dropped, BRIO rounds of Table 2, Moore
+// index of the 21-bit quantised coordinates, ties by index), computed with T threads.
+void parallel_order(const double* xyz, int64_t n, uint64_t seed, int T, std::vector<uint32_t>& seq,
+                    std::vector<uint8_t>& rounds) {
+  // duplicates: sort by coordinates, then index; the first of a run represents it
+  std::vector<uint32_t> idx(n);
+  std::iota(idx.begin(), idx.end(), 0u);
+  parallel_sort(idx, T, [&](uint32_t a, uint32_t b) {
+    for (int k = 0; k < 3; ++k)
+      if (xyz[3 * (size_t)a + k] != xyz[3 * (size_t)b + k]) return xyz[3 * (size_t)a + k] < xyz[3 * (size_t)b + k];
+    return a < b;
+  });
+  std::vector<uint8_t> dup(n, 0);
+  for (int64_t s = 1; s < n; ++s) {
+    const double* p = xyz + 3 * (size_t)idx[s];
+    const double* q = xyz + 3 * (size_t)idx[s - 1];
+    if (p[0] == q[0] && p[1] == q[1] && p[2] == q[2]) dup[idx[s]] = 1;
+  }
+  // Moore keys on the box of all points
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      mn[k] = std::min(mn[k], xyz[3 * i + k]);
+      mx[k] = std::max(mx[k], xyz[3 * i + k]);
+    }
+  double scale[3];
+  for (int k = 0; k < 3; ++k) scale[k] = mx[k] - mn[k] > 0.0 ? 2097152.0 / (mx[k] - mn[k]) : 0.0;
+  std::vector<uint64_t> key(n), h(n);
+  parallel_for((size_t)n, T, [&](size_t a, size_t b) {
+    for (size_t i = a; i < b; ++i) {
+      uint32_t q[3];
+      for (int k = 0; k < 3; ++k) {
+        double f = std::floor((xyz[3 * i + k] - mn[k]) * scale[k]);
+        if (f < 0.0) f = 0.0;
+        if (f > 2097151.0) f = 2097151.0;
+        q[k] = (uint32_t)f;
+      }
+      key[i] = moore_index(q[0], q[1], q[2], kLevels);
+      h[i] = brio_hash(seed, (uint64_t)i);
+    }
+  });
+  // BRIO rounds from the rank of the hash
+  std::iota(idx.begin(), idx.end(), 0u);
+  parallel_sort(idx, T, [&](uint32_t a, uint32_t b) { return h[a] != h[b] ? h[a] < h[b] : a < b; });
+  rounds.assign(n, 0);
+  parallel_for((size_t)n, T, [&](size_t a, size_t b) {
+    for (size_t rank = a; rank < b; ++rank) {
+      int r = 0;
+      uint64_t end = 2048;
+      while (rank >= end) {
+        ++r;
+        end *= 7;
+      }
+      rounds[idx[rank]] = (uint8_t)r;
+    }
+  });
+  // order by (round, key, index), duplicates left out
+  std::iota(idx.begin(), idx.end(), 0u);
+  parallel_sort(idx, T, [&](uint32_t a, uint32_t b) {
+    if (rounds[a] != rounds[b]) return rounds[a] < rounds[b];
+    if (key[a] != key[b]) return key[a] < key[b];
+    return a < b;
+  });
+  seq.clear();
+  seq.reserve(n);
+  for (uint32_t i : idx)
+    if (!dup[i]) seq.push_back(i);
+}
 
 struct ParStats {
   int64_t passes = 0, aborted = 0, sequential_passes = 0, max_threads = 0;
@@ -383,15 +494,9 @@ int64_t delaunay_parallel(const double* xyz, int64_t n, uint64_t seed, int threa
                           uint32_t* out, int64_t cap, int64_t* stats) {
   if (n < 0 || (n > 0 && !xyz) || n >= (int64_t)0xFFFFFFF0 || threads < 1 || min_per_thread < 1) return ORACLE_EINVAL;
   if (!finite_input(xyz, n)) return ORACLE_EINVAL;
-  std::vector<int64_t> rep;
-  dedup(xyz, n, rep);
-  std::vector<int64_t> order;
-  insertion_order(xyz, n, seed, order);
-  std::vector<uint8_t> rounds(n);
-  brio_rounds(n, seed, rounds.data());
   std::vector<uint32_t> seq;
-  for (int64_t i : order)
-    if (rep[i] == i) seq.push_back((uint32_t)i);
+  std::vector<uint8_t> rounds;
+  parallel_order(xyz, n, seed, threads, seq, rounds);
   if (seq.size() < 4) return ORACLE_EDEGENERATE;
   PMesh M;
   M.xyz = xyz;
@@ -400,14 +505,16 @@ int64_t delaunay_parallel(const double* xyz, int64_t n, uint64_t seed, int threa
   M.N.reset(new std::atomic<uint32_t>[4 * M.cap]);
   M.alive.reset(new std::atomic<uint8_t>[M.cap]);
   M.stamp.reset(new uint64_t[M.cap]);
-  for (uint64_t s = 0; s < M.cap; ++s) {
-    for (int k = 0; k < 4; ++k) {
-      M.V[4 * s + k].store(0, std::memory_order_relaxed);
-      M.N[4 * s + k].store(NONE, std::memory_order_relaxed);
+  parallel_for(M.cap, threads, [&](size_t a, size_t b) {
+    for (size_t s = a; s < b; ++s) {
+      for (int k = 0; k < 4; ++k) {
+        M.V[4 * s + k].store(0, std::memory_order_relaxed);
+        M.N[4 * s + k].store(NONE, std::memory_order_relaxed);
+      }
+      M.alive[s].store(0, std::memory_order_relaxed);
+      M.stamp[s] = 0;
     }
-    M.alive[s].store(0, std::memory_order_relaxed);
-    M.stamp[s] = 0;
-  }
+  });
   M.tag.reset(new std::atomic<uint64_t>[n]);
   for (int64_t i = 0; i < n; ++i) M.tag[i].store(0, std::memory_order_relaxed);
   // Init (Section 2.1), as the serial oracle: the first four non-coplanar points of the order
@@ -475,17 +582,28 @@ int64_t delaunay_parallel(const double* xyz, int64_t n, uint64_t seed, int threa
     rc = insert_parallel(M, W, std::move(todo), r == 0 ? 1 : threads, min_per_thread, mn, ext, seed, &pass, ps);
   }
   if (rc != ORACLE_OK) return rc;
-  std::vector<std::array<uint32_t, 4>> tets;
+  // output: the finite live tetrahedra, canonical and sorted (threads over slot ranges)
   const uint64_t used = std::min<uint64_t>(M.bump.load(), M.cap);
-  for (uint64_t s = 0; s < used; ++s) {
-    if (!M.alive[s].load(std::memory_order_relaxed)) continue;
-    uint32_t v[4];
-    M.getv((uint32_t)s, v);
-    if (gpos4(v) >= 0) continue;
-    canonical(v);
-    tets.push_back({v[0], v[1], v[2], v[3]});
+  std::vector<std::vector<std::array<uint32_t, 4>>> part(threads);
+  {
+    std::vector<std::thread> th;
+    auto collect = [&](int w) {
+      for (uint64_t s = used * w / threads; s < used * (w + 1) / threads; ++s) {
+        if (!M.alive[s].load(std::memory_order_relaxed)) continue;
+        uint32_t v[4];
+        M.getv((uint32_t)s, v);
+        if (gpos4(v) >= 0) continue;
+        canonical(v);
+        part[w].push_back({v[0], v[1], v[2], v[3]});
+      }
+    };
+    for (int w = 1; w < threads; ++w) th.emplace_back(collect, w);
+    collect(0);
+    for (auto& x : th) x.join();
   }
-  sort_tets(tets);
+  std::vector<std::array<uint32_t, 4>> tets;
+  for (auto& v : part) tets.insert(tets.end(), v.begin(), v.end());
+  parallel_sort(tets, threads, [](const std::array<uint32_t, 4>& a, const std::array<uint32_t, 4>& b) { return a < b; });
   if (stats) {
     int64_t walk = 0, cav = 0, ball = 0;
     for (auto& X : W) walk += X.walk, cav += X.cav, ball += X.ball;

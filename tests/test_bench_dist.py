@@ -48,3 +48,20 @@ def test_replicas_draw_independent_clouds():
     from paper_1805_08831_gb300 import synth
     a, b = synth.make("uniform", 1000, 2), synth.make("uniform", 1000, 3)
     assert a.shape == b.shape and not (a == b).all()
+
+
+def test_cpu_paper_scheme_leg_reports_an_exact_rate():
+    """The bench's second host baseline on a small sample: every host core, tetrahedra equal to
+    the serial oracle's, and a rate computed from them."""
+    import numpy as np
+
+    import bench
+    import oracle
+    from paper_1805_08831_gb300 import synth
+    x = synth.uniform_cube(20000, 2)
+    ref, _ = oracle.delaunay(x, seed=bench.SEED)
+    leg = bench.cpu_paper_scheme(x, ref)
+    assert "error" not in leg, leg
+    assert leg["bit_exact_vs_oracle"] is True and leg["cores"] == (os.cpu_count() or 1)
+    assert leg["value"] > 0 and leg["unit"] == "Mtets/s" and leg["passes"] >= 3
+    assert np.isfinite(leg["value"])

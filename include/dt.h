@@ -46,7 +46,8 @@ extern "C" {
 #define DT_ESTATE (-7)      /* call not valid in the handle's current state */
 
 #define DT_SCHED_PLAIN 0    /* Moore segments + rescaling/shift re-partition (Section 3.3) */
-#define DT_SCHED_LEARNED 1  /* segments sized by the learned cavity/conflict model */
+#define DT_SCHED_LEARNED 1  /* claim ranks from the learned cavity-size model (a loaded model is
+                               required, dt_load_model); the same tetrahedra as the plain schedule */
 
 #define DT_FLAG_NO_CANONICAL_SORT 1u /* dt_get_tets(canonical=1) rotates but does not sort */
 #define DT_FLAG_PROFILE 2u           /* time each launch of the round kernels with CUDA events */

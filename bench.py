@@ -7,6 +7,9 @@ uniform in the unit cube (float64). `value` is device time measured with CUDA ev
 library's stream; `e2e` repeats the step through the host entry points with the copies in.
 `--impl reference` times the serial CPU oracle (the reference arm) on a bounded sample.
 Multi-GPU runs are replicas (one independent cloud per rank; a single cloud does not shard).
+The default line also carries the CPU legs (the serial oracle, and the paper's CPU thread scheme
+on every host core, both on the first 1e6 points) and the other rows of the path: the batched
+form, the learned schedule against the plain one, and Delaunay refinement of a box.
 """
 from __future__ import annotations
 
@@ -28,7 +31,7 @@ import numpy as np  # noqa: E402
 from paper_1805_08831_gb300 import synth  # noqa: E402
 
 METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, bit-exact"
-# DRAM bytes (read + write) per candidate of k_insert<0>, from one ncu capture of its longest
+# DRAM bytes (read + write) per candidate of k_insert<0>, from one ncu capture of a large
 # launch at 2e6 uniform points (profiles/k_insert_uniform_2e6.md), and the hash of the kernel
 # sources it was taken on: the traffic is reported only while the sources are unchanged.
 INSERT_TRAFFIC_PER_CANDIDATE = 6547.2

@@ -32,7 +32,7 @@ from paper_1805_08831_gb300 import synth  # noqa: E402
 
 METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, bit-exact"
 # DRAM bytes (read + write) per candidate of k_insert<0>, from one ncu capture of a large
-# launch at 2e6 uniform points (profiles/k_insert_uniform_2e6.md), and the hash of the kernel
+# launch at 2e6 uniform points (the k_insert summary under profiles/), and the hash of the kernel
 # sources it was taken on: the traffic is reported only while the sources are unchanged.
 INSERT_TRAFFIC_PER_CANDIDATE = 6547.2
 INSERT_TRAFFIC_SOURCES = "3b8b85bf491cb6cb"

@@ -244,9 +244,10 @@ const char* dt_strerror(int code);
 
 /* The spatial order of dt_get_order (Moore keys, BRIO rounds, insertion permutation) computed
  * without allocating any device memory. The paper has no counterpart; this entry point exists
- * for callers that cannot call cudaMalloc: code that runs while a CUDA stream is being captured
- * into a graph, hosts whose device memory is all owned by another allocator, and latency-bound
- * callers that cannot pay cudaMalloc's implicit device synchronisation.
+ * for callers that cannot call cudaMalloc: hosts whose device memory is all owned by another
+ * allocator (a framework's caching pool or a fixed arena that may not be bypassed), and code
+ * under a device-memory budget that a new allocation could break. The call synchronises its
+ * stream before it returns (it reads back the coordinate check).
  *  - xyz_dev: [n, 3] float64 row-major (device); n <= DT_NOALLOC_MAX_POINTS, else DT_EINVAL.
  *  - keys_dev [n] uint64, perm_dev [n] uint32, rounds_dev [n] uint8: device outputs, owned by
  *    the caller; same values as dt_get_order after dt_insert of the same points and seed.
@@ -257,7 +258,8 @@ const char* dt_strerror(int code);
  * before any stream capture begins. All calls share the array and each leaves its contents
  * behind (the parts that must start at zero are cleared at the start of every call): calls
  * that overlap on the GPU, from several host threads or streams, race and must be serialised
- * by the caller. Errors: DT_EINVAL (bad pointer, size over the limit, non-finite or
+ * by the caller. The looked-up address is kept for the life of the process: do not use this
+ * entry point after cudaDeviceReset on that device. Errors: DT_EINVAL (bad pointer, size over the limit, non-finite or
  * |x| > 1e30 coordinate), DT_ECUDA. */
 int dt_order_noalloc(const double* xyz_dev, uint64_t n, uint64_t seed, uint64_t* keys_dev, uint32_t* perm_dev,
                      uint8_t* rounds_dev, void* stream);

@@ -6,7 +6,11 @@ Plain float64 numpy, written from the definitions, sharing no code with the CUDA
     W2[32][32], b2[32], W3[32][2], b3[2], W[i][j] = input i -> output j);
   * its loss per sample, (o0 - y0)^2 + softplus(o1) - y1 * o1, averaged, and the gradient of
     that mean by backpropagation written out layer by layer;
-  * the eight per-point features of the scheduler from a point set in insertion order.
+  * the eight per-point features of the scheduler from a point set in insertion order;
+  * training: Adam with bias correction (Kingma and Ba, "Adam: a method for stochastic
+    optimization", ICLR 2015, Algorithm 1; beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on
+    minibatches drawn with replacement by a counter-based SplitMix64 hash (Steele, Lea and
+    Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014).
 The paper has no learned component; these definitions are the repository's own (the scheduler
 only reorders insertions, so the tetrahedra never depend on them).
 """
@@ -131,3 +135,54 @@ def features(xyz_sorted, keys_sorted, rounds_sorted, dup_sorted, bbox):
                   (nc - mean) / (1 + nc + mean), ((key >> 57) & 63) / 64, ((key >> 51) & 63) / 64,
                   int(rounds_sorted[s]) / 8, 2 * min(min(u[s, k], 1 - u[s, k]) for k in range(3))]
     return out
+
+
+# ------------------------------------------------------------------ training
+_MASK64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15  # SplitMix64's increment
+_STEP_SALT = 0x51ED2701        # per-step seed offset of the minibatch draw
+
+
+def splitmix64_mix(z: int) -> int:
+    """SplitMix64's output function (Steele, Lea, Flood 2014) on one 64-bit integer."""
+    z &= _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def draw_indices(n: int, batch: int, seed: int) -> np.ndarray:
+    """Minibatch of `batch` sample indices in [0, n), with replacement: index k is
+    mix(seed + (k + 1) * golden) mod n, i.e. output k of a SplitMix64 stream started at seed."""
+    return np.array([splitmix64_mix(seed + (k + 1) * _GOLDEN) % n for k in range(batch)], dtype=np.int64)
+
+
+def adam_step(params, grad, m, v, lr: float, t: int, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam update at step t >= 1 (Kingma and Ba 2015, Algorithm 1):
+    m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
+    p <- p - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  Returns (p, m, v)."""
+    g = np.asarray(grad, dtype=np.float64)
+    m = b1 * np.asarray(m, dtype=np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, dtype=np.float64) + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    p = np.asarray(params, dtype=np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return p, m, v
+
+
+def train(params, x, y, steps: int, batch: int, lr: float, seed: int):
+    """`steps` Adam steps from zero moments; step t (0-based) draws its minibatch with seed
+    seed + (t + 1) * 0x51ED2701 (mod 2^64) and takes the gradient of the minibatch's mean loss.
+    Returns (params, per-step minibatch losses)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    p = np.asarray(params, dtype=np.float64).copy()
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    losses = []
+    for t in range(steps):
+        idx = draw_indices(len(x), batch, (seed + (t + 1) * _STEP_SALT) & _MASK64)
+        L, g = loss_grad(p, x[idx], y[idx])
+        losses.append(L)
+        p, m, v = adam_step(p, g, m, v, lr, t + 1)
+    return p, np.array(losses)

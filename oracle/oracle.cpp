@@ -801,6 +801,13 @@ int64_t delaunay(const double* xyz, int64_t n, uint64_t seed, const int64_t* ord
   if (seq.size() < 4) return ORACLE_EDEGENERATE;
   Mesh M;
   M.xyz = xyz;
+  // Storage only: a uniform cloud ends with about 6.8 slots per point; reserving them up front
+  // keeps a 1e8-point run from doubling its vectors past the host's memory.
+  const size_t slots_hint = 7 * seq.size() + 64;
+  M.v.reserve(slots_hint);
+  M.n.reserve(slots_hint);
+  M.alive.reserve(slots_hint);
+  M.stamp.reserve(slots_hint);
   size_t k2 = 2;
   while (k2 < seq.size() && collinear_exact(M.P(seq[0]), M.P(seq[1]), M.P(seq[k2]))) ++k2;
   if (k2 >= seq.size()) return ORACLE_EDEGENERATE;
@@ -834,9 +841,6 @@ int64_t delaunay(const double* xyz, int64_t n, uint64_t seed, const int64_t* ord
     int rc = I.insert(seq[q]);
     if (rc != ORACLE_OK) return rc;
   }
-  std::vector<std::array<uint32_t, 4>> tets;
-  for (uint32_t t = 0; t < M.v.size(); ++t)
-    if (M.alive[t] && M.gpos(t) < 0) tets.push_back(M.v[t]);
   int64_t ghosts = 0, hullv = 0;
   int64_t flags = 0;
   if (do_validate) flags = validate(M, &ghosts, &hullv);
@@ -851,7 +855,26 @@ int64_t delaunay(const double* xyz, int64_t n, uint64_t seed, const int64_t* ord
     st->n_ghosts = ghosts;
     st->n_hull_vertices = hullv;
   }
-  return write_out(tets, out, cap, st);
+  // Output: the finite tetrahedra go straight into the caller's buffer, canonical and sorted
+  // there, after the mesh is released (storage only; the same list as collecting them first).
+  int64_t T = 0;
+  for (uint32_t t = 0; t < M.v.size(); ++t)
+    if (M.alive[t] && M.gpos(t) < 0) ++T;
+  if (st) st->n_tets = T;
+  if (T > cap || !out) return ORACLE_ETOOSMALL;
+  int64_t w = 0;
+  for (uint32_t t = 0; t < M.v.size(); ++t)
+    if (M.alive[t] && M.gpos(t) < 0) {
+      for (int k = 0; k < 4; ++k) out[4 * w + k] = M.v[t][k];
+      canonical(out + 4 * w);
+      ++w;
+    }
+  { Mesh empty; std::swap(M.v, empty.v); std::swap(M.n, empty.n); std::swap(M.alive, empty.alive);
+    std::swap(M.stamp, empty.stamp); }
+  static_assert(sizeof(std::array<uint32_t, 4>) == 16, "rows are four packed ids");
+  auto* rows = reinterpret_cast<std::array<uint32_t, 4>*>(out);
+  std::sort(rows, rows + T);
+  return T;
 }
 
 int64_t brute_force(const double* xyz, int64_t n, uint32_t* out, int64_t cap) {

@@ -540,9 +540,11 @@ uint64_t brio_round_end(int r) {
   return e;
 }
 
-uint64_t radix_hist_entries(uint64_t n) {
+// Histogram and scan entries of one radix sort of n keys (compile-time, so fixed scratch areas
+// can be checked against it).
+constexpr uint64_t radix_hist_entries_for(uint64_t n) {
   uint64_t tiles = (n + kTile - 1) / kTile;
-  uint64_t len = 256 * std::max<uint64_t>(tiles, 1);
+  uint64_t len = 256 * (tiles > 1 ? tiles : 1);
   uint64_t extra = 0, l = len;
   while (l > 1) {
     l = (l + kScanTile - 1) / kScanTile;
@@ -550,6 +552,8 @@ uint64_t radix_hist_entries(uint64_t n) {
   }
   return len + extra + 64;
 }
+
+uint64_t radix_hist_entries(uint64_t n) { return radix_hist_entries_for(n); }
 
 bool radix_sort_pairs(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int bits,
                       uint32_t* hist, cudaStream_t s) {
@@ -718,7 +722,7 @@ namespace dtg {
 namespace {
 
 constexpr uint64_t kNoAllocMax = DT_NOALLOC_MAX_POINTS;
-constexpr uint64_t kNoAllocHist = (256ull * ((kNoAllocMax + 4095) / 4096)) + 1024;
+constexpr uint64_t kNoAllocHist = radix_hist_entries_for(kNoAllocMax);
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffK0 = 0;
 constexpr size_t kOffK1 = kOffK0 + align256(kNoAllocMax * 8);

@@ -1,8 +1,19 @@
-"""The bench's workload at full size (1e7 uniform points, seed 2, the bench's launch settings),
-checked by what holds at any size: every facet is shared by at most two tetrahedra, the
-triangulation is a topological ball (Euler characteristic 1), and sampled tetrahedra are
-positively oriented with an empty circumsphere against all 1e7 points (the oracle's exact
-predicates decide the points that lie near a sphere)."""
+"""Full-size workloads on the GPU.
+
+* Bit-exact parity by digest: the canonical tetrahedron list of each full-size workload
+  (1e7 uniform, 1e7 degenerate mix, 1e8 uniform, 1e8 cube + slab) hashes to the SHA-256 the serial
+  CPU oracle's list of the same seeded input hashes to (tests/golden/fullsize.json, written by
+  tests/golden/make_fullsize.py, which calls only the oracle). On a mismatch the per-chunk digests
+  locate the first differing block of rows.
+* The bench's workload (1e7 uniform points, seed 2) is also checked by what holds at any size:
+  every facet is shared by at most two tetrahedra, the triangulation is a topological ball
+  (Euler characteristic 1), and sampled tetrahedra are positively oriented with an empty
+  circumsphere against all 1e7 points (the oracle's exact predicates decide the points that lie
+  near a sphere)."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +27,34 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1805_08831_gb300 as dt  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fullsize.json")
+with open(GOLDEN) as _f:
+    FULLSIZE = json.load(_f)
+
+
+@pytest.mark.parametrize("name", ["uniform_1e7", "degenerate_1e7", "uniform_1e8", "slab_1e8"])
+def test_fullsize_canonical_list_matches_the_oracle_digest(name):
+    rec = FULLSIZE[name]
+    x = synth.make(rec["kind"], rec["n"], rec["seed"])
+    with dt.Triangulation(seed=rec["seed"]) as t:
+        t.insert(torch.from_numpy(x).cuda())
+        st = t.stats()
+        del x
+        tets = t.tets(canonical=True).cpu().numpy().view(np.uint32)
+    assert st["n_dups"] == rec["n_dups"]
+    assert len(tets) == rec["n_tets"]
+    t = np.ascontiguousarray(tets, dtype="<u4")
+    digest = hashlib.sha256(memoryview(t).cast("B")).hexdigest()
+    if digest != rec["sha256"]:
+        rows = rec["chunk_rows"]
+        for k, want in enumerate(rec["chunks"]):
+            got = hashlib.sha256(memoryview(t[k * rows:(k + 1) * rows]).cast("B")).hexdigest()
+            if got != want:
+                pytest.fail(f"{name}: first differing block of rows starts at {k * rows}; "
+                            f"GPU rows there: {t[k * rows:k * rows + 4].tolist()}")
+        pytest.fail(f"{name}: digest differs but no block does")
+    assert t[:4].tolist() == rec["first_rows"] and t[-4:].tolist() == rec["last_rows"]
 
 
 def test_uniform_1e7_is_a_delaunay_ball():

@@ -44,6 +44,40 @@ def test_gradient_matches_oracle(n):
     assert np.max(np.abs(g - ref)) <= 1e-4 * np.max(np.abs(ref)) + 1e-7
 
 
+@pytest.mark.parametrize("steps", [1, 4])
+def test_training_matches_oracle(steps):
+    """dt_mlp_train (minibatch draw, FP32 gradient, Adam) against the float64 training oracle.
+
+    The per-step minibatch losses depend on which samples the counter-based draw picks: they
+    must agree to FP32 accuracy (1e-5 relative). Adam moves each parameter by about lr per step
+    whatever the gradient's size, so parameters whose gradient is small enough for FP32 rounding
+    to flip its sign may differ by up to 2 lr per step; all others must agree within 2 % of lr
+    per step, and every parameter within the largest Adam move, 3.2 lr per step."""
+    params, x, y = problem(40 + steps, 4096)
+    lr, batch, seed = 1e-3, 256, 2 ** 40 + 17
+    p = torch.from_numpy(params.copy()).cuda()
+    losses = dt.mlp_train(p, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), steps=steps, batch=batch,
+                          lr=lr, seed=seed)
+    ref_p, ref_losses = OL.train(params.astype(np.float64), x.astype(np.float64), y.astype(np.float64),
+                                 steps=steps, batch=batch, lr=lr, seed=seed)
+    assert np.allclose(losses, ref_losses, rtol=1e-5, atol=1e-6)
+    got = p.cpu().numpy().astype(np.float64)
+    diff = np.abs((got - params) - (ref_p - params))
+    # well-conditioned parameters: the gradient of every step is far from zero
+    well = np.ones(len(params), dtype=bool)
+    q = params.astype(np.float64)
+    m = np.zeros_like(q)
+    v = np.zeros_like(q)
+    for t in range(steps):
+        idx = OL.draw_indices(len(x), batch, (seed + (t + 1) * 0x51ED2701) % 2 ** 64)
+        _, g = OL.loss_grad(q, x[idx].astype(np.float64), y[idx].astype(np.float64))
+        well &= np.abs(g) > 1e-3 * np.max(np.abs(g))
+        q, m, v = OL.adam_step(q, g, m, v, lr, t + 1)
+    assert well.mean() > 0.5
+    assert np.max(diff[well]) <= 0.02 * lr * steps
+    assert np.max(diff) <= 3.2 * lr * steps + 1e-7
+
+
 def test_training_fits_a_teacher_network():
     """Targets produced by a fixed random network are learnable: the loss falls well below the
     loss of the initial parameters (training runs entirely in the library's kernels)."""

@@ -1,11 +1,11 @@
 """dt_order_noalloc: the spatial order (Moore keys, BRIO rounds, insertion permutation) computed
 without allocating device memory.
 
-Some callers cannot call cudaMalloc: code that runs while a stream is captured into a CUDA
-graph, hosts whose device memory all belongs to another allocator, and latency-bound paths that
-cannot pay for cudaMalloc's implicit synchronisation. This entry point serves them from one
-file-scope device array. It must give exactly the keys, permutation and rounds of the ordinary
-(allocating) path, on two calls in a row that reuse that array.
+Some callers cannot call cudaMalloc: hosts whose device memory all belongs to another allocator
+(a framework's caching pool or a fixed arena), and code under a device-memory budget that a new
+allocation could break. This entry point serves them from one file-scope device array. It must
+give exactly the keys, permutation and rounds of the ordinary (allocating) path, on two calls in
+a row that reuse that array, and leave the device's free memory unchanged.
 """
 import ctypes
 
@@ -22,20 +22,11 @@ if not torch.cuda.is_available():
 
 import paper_1805_08831_gb300 as dt  # noqa: E402
 
+DT_NOALLOC_MAX_POINTS = 262144  # the limit include/dt.h declares for dt_order_noalloc
+
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
-
-
-def order_without_allocation(x, seed):
-    n = len(x)
-    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    keys = torch.empty(n, dtype=torch.int64, device="cuda")
-    perm = torch.empty(n, dtype=torch.int32, device="cuda")
-    rounds = torch.empty(n, dtype=torch.uint8, device="cuda")
-    rc = dt.lib().dt_order_noalloc(_ptr(xt), n, seed, _ptr(keys), _ptr(perm), _ptr(rounds), None)
-    return (rc, keys.cpu().numpy().view(np.uint64), perm.cpu().numpy().view(np.uint32),
-            rounds.cpu().numpy())
 
 
 def order_with_allocation(x, seed):
@@ -45,11 +36,29 @@ def order_with_allocation(x, seed):
 
 
 def test_order_without_allocation_matches_the_allocating_path_twice():
+    # a first call loads the library's kernels and its scratch array (lazy module loading
+    # allocates device memory for code once); the two measured calls after it allocate nothing
+    w = torch.from_numpy(synth.uniform_cube(1000, 1)).cuda()
+    wk = torch.empty(1000, dtype=torch.int64, device="cuda")
+    wp = torch.empty(1000, dtype=torch.int32, device="cuda")
+    wr = torch.empty(1000, dtype=torch.uint8, device="cuda")
+    assert dt.lib().dt_order_noalloc(_ptr(w), 1000, 1, _ptr(wk), _ptr(wp), _ptr(wr), None) == dt.DT_OK
     for call, (n, seed) in enumerate([(50000, 3), (120001, 9)]):
         x = synth.uniform_cube(n, 40 + call)
         x[10:20] = x[:10]  # duplicates must not disturb the order
-        rc, keys, perm, rounds = order_without_allocation(x, seed)
+        xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        keys_t = torch.empty(n, dtype=torch.int64, device="cuda")
+        perm_t = torch.empty(n, dtype=torch.int32, device="cuda")
+        rounds_t = torch.empty(n, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        rc = dt.lib().dt_order_noalloc(_ptr(xt), n, seed, _ptr(keys_t), _ptr(perm_t), _ptr(rounds_t), None)
+        free_after = torch.cuda.mem_get_info()[0]
         assert rc == dt.DT_OK
+        assert free_after == free_before  # nothing was allocated on the device
+        keys = keys_t.cpu().numpy().view(np.uint64)
+        perm = perm_t.cpu().numpy().view(np.uint32)
+        rounds = rounds_t.cpu().numpy()
         ref_keys, ref_perm, ref_rounds = order_with_allocation(x, seed)
         assert np.array_equal(keys, ref_keys)
         assert np.array_equal(perm, ref_perm)
@@ -57,7 +66,7 @@ def test_order_without_allocation_matches_the_allocating_path_twice():
 
 
 def test_order_without_allocation_rejects_sizes_over_its_limit():
-    n = dt.lib() and 262144 + 1
+    n = DT_NOALLOC_MAX_POINTS + 1
     xt = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
     out = torch.empty(8, dtype=torch.int64, device="cuda")
     rc = dt.lib().dt_order_noalloc(_ptr(xt), n, 0, _ptr(out), _ptr(out), _ptr(out), None)

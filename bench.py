@@ -31,13 +31,14 @@ import numpy as np  # noqa: E402
 from paper_1805_08831_gb300 import synth  # noqa: E402
 
 METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, bit-exact"
-# DRAM bytes (read + write) per candidate of k_insert<0>, from one ncu capture of a large
-# launch at 2e6 uniform points (the k_insert summary under profiles/), and the hash of the kernel
+# DRAM bytes (read + write) per insertion of the asynchronous insertion kernel, from one ncu
+# capture of a large launch (the k_async summary under profiles/), and the hash of the kernel
 # sources it was taken on: the traffic is reported only while the sources are unchanged.
-INSERT_TRAFFIC_PER_CANDIDATE = 6547.2
-INSERT_TRAFFIC_SOURCES = "3b8b85bf491cb6cb"
+ASYNC_TRAFFIC_PER_INSERTION = None
+ASYNC_TRAFFIC_SOURCES = ""
 REFINE_K = 128  # the refinement workload: the unit cube at size 1/128 from its surface lattice
-KERNEL_SOURCES = ["engine.cuh", "dt.cu", "common.cuh", "predicates.cuh"]
+KERNEL_SOURCES = ["async.cu", "engine.cuh", "dt.cu", "common.cuh", "predicates.cuh"]
+GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize.json")
 PAPER_1E7_EPYC = 31.3  # Fig. 9, AMD EPYC 7551, 1e7 uniform points (context)
 SEED = 2
 
@@ -144,26 +145,91 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_bytes(st):
-    """Algorithmic bytes of each round kernel over the run, from the measured C, F, walk steps.
-
-    tetrahedron record 32 B, point 24 B, claim word 8 B (an atomic reads and writes it),
-    index 4 B. Per inserted point with |C| = C, |B| = F, boundary vertices V = F/2 + 2:
-      walk:   per attempt 4 points + 1 record, per step 1 record + 1 new point
-      cavity: records of C and its outside neighbours (F), points of V, claims of C + F,
-              C + F indices out
-      insert: C + F indices in, claims of C + F read, F records read and written, F
-              back-pointers, C freed slots
-    Work of attempts that lost a conflict is overhead, not algorithmic bytes.
-    """
+def path_bytes(st):
+    """Algorithmic bytes per inserted point, the terms of the hot-path table's formula
+    (tetrahedron record 32 B, point 24 B, claim or lock word 8 B read and written, index 4 B),
+    from the run's measured |C| = C, |B| = F, boundary vertices V = F/2 + 2 and walk steps w:
+      walk (S7):            w (32 + 72)            a record and three points per step
+      cavity (S8):          (C + F) 32 + (V + F) 24 + (C + F) 8
+      ball (S9-S10):        F 32 + F 4 + C 4 + (C + F) 4
+    Work of attempts that lost or restarted is overhead, not algorithmic bytes."""
     ins = max(st["n_unique"], 1)
     C = st["sum_cavity"] / ins
     F = st["sum_ball"] / ins
     V = F / 2 + 2
-    walk = st["n_attempts"] * (4 * 24 + 32) + st["sum_walk"] * (32 + 24)
-    cavity = ins * (32 * (C + F) + 24 * V + 16 * (C + F) + 4 * (C + F))
-    insert = ins * (4 * (C + F) + 8 * (C + F) + 32 * F + 32 * F + 4 * F)
-    return {"walk": walk, "cavity": cavity, "insert": insert}, {"C": C, "F": F, "V": V}
+    w = st["sum_walk"] / max(st["n_attempts"], 1)
+    terms = {"walk": w * (32 + 72), "cavity": (C + F) * 32 + (V + F) * 24 + (C + F) * 8,
+             "ball": F * 32 + F * 4 + C * 4 + (C + F) * 4}
+    return terms, {"C": C, "F": F, "V": V, "w": w}
+
+
+def load_golden(name):
+    try:
+        with open(GOLDEN) as f:
+            return json.load(f).get(name)
+    except Exception:
+        return None
+
+
+def canonical_digest(tri):
+    """SHA-256 of the handle's canonical tetrahedron list (little-endian [T, 4] uint32) and T."""
+    import hashlib
+    t = np.ascontiguousarray(tri.tets(canonical=True).cpu().numpy().view(np.uint32), dtype="<u4")
+    return hashlib.sha256(memoryview(t).cast("B")).hexdigest(), int(len(t))
+
+
+def digest_check(tri, name):
+    """Bit-exact flag of the whole canonical list against the oracle's digest of the same
+    workload (tests/golden/fullsize.json), or None when no digest is stored for it."""
+    rec = load_golden(name)
+    if rec is None:
+        return None
+    d, T = canonical_digest(tri)
+    return bool(d == rec["sha256"] and T == rec["n_tets"])
+
+
+def golden_name(kind, n, seed):
+    for name in ("uniform_1e7", "degenerate_1e7", "uniform_1e8", "slab_1e8"):
+        rec = load_golden(name)
+        if rec and rec["kind"] == kind and rec["n"] == int(n) and rec["seed"] == seed:
+            return name
+    return None
+
+
+def roofline_of(st_prof, steps_prof, ms_step, peak, peak_kind):
+    """The dominant kernel's achieved bandwidth against HBM from a profiled run: its algorithmic
+    bytes per launch (path_bytes' terms of the steps it performs x the insertions it made) over
+    its mean launch time. The asynchronous kernel performs walk, cavity and ball of every point
+    it inserts; the round-based kernels one step each, for all inserted points."""
+    terms, cfb = path_bytes(st_prof)
+    bpt = sum(terms.values())
+    ins = st_prof["n_unique"]
+    times = {"k_async": st_prof["ms_async"], "k_walk": st_prof["ms_walk"], "k_cavity": st_prof["ms_cavity"],
+             "k_insert": st_prof["ms_insert_k"], "k_cta_insert": st_prof["ms_first_round"]}
+    launches = {"k_async": st_prof["n_async"], "k_walk": st_prof["n_profiled"], "k_cavity": st_prof["n_profiled"],
+                "k_insert": st_prof["n_profiled"], "k_cta_insert": steps_prof}
+    dom = max(("k_async", "k_walk", "k_cavity", "k_insert"), key=lambda k: times[k])
+    if dom == "k_async":
+        alg = bpt * st_prof["n_inserted_async"]
+    else:
+        rest = ins - st_prof["n_inserted_async"]
+        alg = {"k_walk": terms["walk"], "k_cavity": terms["cavity"], "k_insert": terms["ball"]}[dom] * rest
+    ms_dom = times[dom] / steps_prof
+    achieved = alg / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
+    traffic = None
+    if (dom == "k_async" and ASYNC_TRAFFIC_PER_INSERTION is not None
+            and kernel_sources_hash() == ASYNC_TRAFFIC_SOURCES):
+        traffic = ASYNC_TRAFFIC_PER_INSERTION * st_prof["n_inserted_async"] / max(launches[dom] / steps_prof, 1)
+    n_launch = max(launches[dom] / steps_prof, 1)
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+            "alg_bytes_per_launch": alg / n_launch, "ms_per_launch": ms_dom / n_launch,
+            "launches_per_step": n_launch, "share_of_step": ms_dom / ms_step if ms_step else None,
+            "kernel_ms_per_step": {k: v / steps_prof for k, v in times.items()},
+            "bytes_per_point": terms, "path_bytes_per_point": bpt,
+            "path_frac": bpt * ins / (ms_step / 1e3) / 1e9 / peak if ms_step else None,
+            "how": "alg bytes = the hot-path table's per-point terms x insertions of the kernel; time from "
+                   "CUDA events around every launch in a separate profiled run of the same workload"}, cfb
 
 
 def run_oracle(x, seed):
@@ -307,9 +373,10 @@ def timed_inserts(tri, xd, steps, warmup, stream):
     return ms, st, tri.num_tets()
 
 
-def learned_vs_plain(n, steps, warmup, train_steps, params=None):
+def learned_vs_plain(n, steps, warmup, train_steps, params=None, seed=SEED):
     """The cube + slab workload (the learned scheduler's target) with the plain and the learned
-    schedule on the same GPU: same tetrahedra, Mtets/s and conflicts of each."""
+    schedule on the same GPU: Mtets/s, conflicts, the whole path's fraction of the HBM roofline
+    and the bit-exact flag against the oracle's digest, for each."""
     import torch
     import paper_1805_08831_gb300 as dt
     info = {}
@@ -317,19 +384,29 @@ def learned_vs_plain(n, steps, warmup, train_steps, params=None):
         params, losses, train_s = train_scheduler_on_configs(train_steps)
         info.update({"train_s": train_s, "train_steps": train_steps,
                      "train_loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())]})
-    x = synth.cube_and_slab(int(n), SEED)
+    x = synth.cube_and_slab(int(n), seed)
     xd = torch.from_numpy(x).cuda()
+    del x
     stream = torch.cuda.current_stream()
-    for name, sched in (("plain", dt.DT_SCHED_PLAIN), ("learned", dt.DT_SCHED_LEARNED)):
+    peak, _ = load_peaks()
+    name = golden_name("slab", n, seed)
+    for label, sched in (("plain", dt.DT_SCHED_PLAIN), ("learned", dt.DT_SCHED_LEARNED)):
         tri = dt.Triangulation(seed=SEED, stream=stream, schedule=sched)
         if sched == dt.DT_SCHED_LEARNED:
             tri.load_model(params)
         ms, st, T = timed_inserts(tri, xd, steps, warmup, stream)
-        info[name] = {"value": T * len(ms) / (sum(ms) / 1e3) / 1e6, "unit": "Mtets/s",
-                      "ms_per_step": sum(ms) / len(ms), "tets": T, "n_conflicts": st["n_conflicts"],
-                      "n_attempts": st["n_attempts"], "n_rounds": st["n_rounds"], "n_passes": st["n_passes"]}
+        t = sum(ms) / len(ms)
+        terms, _ = path_bytes(st)
+        info[label] = {"value": T / (t / 1e3) / 1e6, "unit": "Mtets/s", "ms_per_step": t, "tets": T,
+                       "n_conflicts": st["n_conflicts"], "n_attempts": st["n_attempts"],
+                       "n_rounds": st["n_rounds"], "n_passes": st["n_passes"], "n_restarts": st["n_restarts"],
+                       "path_frac": sum(terms.values()) * st["n_unique"] / (t / 1e3) / 1e9 / peak,
+                       "bit_exact_full": digest_check(tri, name) if name else None}
         tri.close()
-    info["workload"] = workload_name("slab", n)
+    del xd
+    torch.cuda.empty_cache()
+    info["workload"] = workload_name("slab", n).rsplit(", seed", 1)[0] + f", seed {seed}"
+    info["digest_of"] = name
     info["learned_over_plain"] = info["learned"]["value"] / info["plain"]["value"]
     return info, params
 
@@ -465,8 +542,8 @@ def run_batch(args, rank, world, local, dist):
     e2e_value = T / (statistics.median(e2e_ms) / 1e3) / 1e6 if e2e_ms else None
 
     peak, peak_kind = load_peaks()
-    bytes_k, cfb = kernel_bytes(st)
-    alg = sum(bytes_k.values())
+    terms, cfb = path_bytes(st)
+    alg = sum(terms.values()) * st["n_unique"]
     achieved = alg / (st["ms_insert"] / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "Mtets/s", "n_gpus": world, "steps": args.steps,
@@ -519,6 +596,77 @@ def run_batch(args, rank, world, local, dist):
     return line
 
 
+def timed_steps(tri, xd, steps, stream, clk=None):
+    """Device ms of `steps` dt_clear + dt_insert steps on the library's stream (CUDA events) and
+    the last step's counters."""
+    import torch
+    ms, st = [], None
+    for _ in range(steps):
+        tri.clear()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tri.insert(xd)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        st = tri.stats()
+    return ms, st
+
+
+def profiled(xd, steps, stream, **kw):
+    """A separate run of the same workload with CUDA events around every launch of the round
+    and asynchronous kernels (DT_FLAG_PROFILE): the kernel split and the roofline's times. The
+    timed steps of the line run without these events."""
+    import paper_1805_08831_gb300 as dt
+    tri = dt.Triangulation(seed=SEED, stream=stream, flags=dt.DT_FLAG_PROFILE, **kw)
+    tri.clear()
+    tri.insert(xd)
+    acc = None
+    for _ in range(steps):
+        _, st = timed_steps(tri, xd, 1, stream)
+        if acc is None:
+            acc = dict(st)
+        else:
+            for k in ("ms_walk", "ms_cavity", "ms_insert_k", "ms_async", "ms_first_round", "n_async",
+                      "n_profiled"):
+                acc[k] += st[k]
+    tri.close()
+    return acc
+
+
+def scale_run(kind, n, seed, steps, warmup):
+    """One large workload on its own handle: Mtets/s over `steps` timed steps, the roofline of its
+    dominant kernel, and the bit-exact flag of the whole canonical list against the oracle's
+    digest (tests/golden/fullsize.json)."""
+    import torch
+    import paper_1805_08831_gb300 as dt
+    x = synth.make(kind, int(n), seed)
+    xd = torch.from_numpy(x).cuda()
+    del x
+    stream = torch.cuda.current_stream()
+    tri = dt.Triangulation(seed=SEED, stream=stream)
+    for _ in range(warmup):
+        tri.clear()
+        tri.insert(xd)
+    ms, st = timed_steps(tri, xd, steps, stream)
+    T = tri.num_tets()
+    t = sum(ms) / len(ms)
+    peak, peak_kind = load_peaks()
+    prof = profiled(xd, 1, stream)
+    roof, cfb = roofline_of(prof, 1, t, peak, peak_kind)
+    name = golden_name(kind, n, seed)
+    exact = digest_check(tri, name) if name else None
+    tri.close()
+    del xd
+    torch.cuda.empty_cache()
+    return {"workload": f"{int(n):.0e} points " + workload_name(kind, n).split(" points ", 1)[1].rsplit(", seed", 1)[0]
+            + f", seed {seed}", "value": T / (t / 1e3) / 1e6, "unit": "Mtets/s", "ms_per_step": t,
+            "steps": steps, "tets": T, "roofline_frac": roof["frac"], "path_frac": roof["path_frac"],
+            "dominant_kernel": roof["kernel"], "exact_per_point": st["n_exact"] / max(st["n_unique"], 1),
+            "bit_exact_full": exact, "digest_of": name, "device_bytes_per_point": st["device_bytes"] / n}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -542,12 +690,12 @@ def main():
     x_host = synth.make(args.kind, n, SEED + rank)
     xd = torch.from_numpy(x_host).cuda()
     stream = torch.cuda.current_stream()
-    flags = 0 if args.no_profile else dt.DT_FLAG_PROFILE
     learned_info = None
+    params = None
     if args.schedule == "learned":
         # trained on the GPU on plain round logs, then the same cloud runs with the plain schedule
         params, losses, train_s = train_scheduler_on_configs(args.train_steps)
-        plain = dt.Triangulation(seed=SEED, stream=stream, flags=flags)
+        plain = dt.Triangulation(seed=SEED, stream=stream)
         p_ms, p_st, p_tets = timed_inserts(plain, xd, args.steps, max(1, args.warmup), stream)
         plain.close()
         learned_info = {"train_s": train_s, "train_steps": args.train_steps,
@@ -556,9 +704,9 @@ def main():
                                   "ms_per_step": sum(p_ms) / len(p_ms), "n_conflicts": p_st["n_conflicts"],
                                   "n_attempts": p_st["n_attempts"], "n_rounds": p_st["n_rounds"],
                                   "n_passes": p_st["n_passes"]}}
-    tri = dt.Triangulation(seed=SEED, stream=stream, flags=flags, max_walk_steps=args.max_walk,
-                           schedule=dt.DT_SCHED_LEARNED if args.schedule == "learned" else dt.DT_SCHED_PLAIN)
-    if args.schedule == "learned":
+    sched = dt.DT_SCHED_LEARNED if args.schedule == "learned" else dt.DT_SCHED_PLAIN
+    tri = dt.Triangulation(seed=SEED, stream=stream, max_walk_steps=args.max_walk, schedule=sched)
+    if params is not None:
         tri.load_model(params)
     for _ in range(args.warmup):
         tri.clear()
@@ -570,35 +718,23 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    totals = {"ms_walk": 0.0, "ms_cavity": 0.0, "ms_insert_k": 0.0, "n_profiled": 0}
     launches = 0
     stat_acc = None
     step_ms = []
     with ClockSampler(local) as clk:
         barrier()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
         for _ in range(args.steps):
-            tri.clear()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            tri.insert(xd)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            st = tri.stats()
+            ms1, st = timed_steps(tri, xd, 1, stream)
+            step_ms += ms1
             launches += st["n_launches"]
-            for k in totals:
-                totals[k] += st[k]
             stat_acc = st
-        t_end.record(stream)
         barrier()
     clocks = clk.summary()
     ntet = tri.num_tets()
     ms = sum(step_ms) / len(step_ms)
     total_ms, all_tets, value = job_throughput(dist, sum(step_ms), ntet, args.steps)
+    name = golden_name(args.kind, n, SEED + rank)
+    bit_exact_full = digest_check(tri, name) if (name and rank == 0) else None
 
     # end to end through the host entry points: pinned input in, tetrahedra out
     pinned = torch.from_numpy(x_host).pin_memory()
@@ -622,27 +758,12 @@ def main():
         e2e_value = float(v[0])
 
     peak, peak_kind = load_peaks()
-    bytes_k, cfb = kernel_bytes(stat_acc)
-    times_k = {"walk": totals["ms_walk"], "cavity": totals["ms_cavity"], "insert": totals["ms_insert_k"]}
     roofline = None
-    if totals["n_profiled"]:
-        dom = max(times_k, key=lambda k: times_k[k])
-        per_step_ms = times_k[dom] / args.steps
-        achieved = bytes_k[dom] / (per_step_ms / 1e3) / 1e9
-        traffic = None
-        cand_per_launch = stat_acc["n_attempts"] / max(stat_acc["n_rounds"], 1)
-        if dom == "insert" and kernel_sources_hash() == INSERT_TRAFFIC_SOURCES:
-            # the capture's bytes per candidate, scaled to this workload's mean candidates per round
-            traffic = INSERT_TRAFFIC_PER_CANDIDATE * cand_per_launch
-        roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
-                    "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                    "traffic": traffic, "traffic_how": "ncu dram bytes per candidate of k_insert<0> (a large launch at 2e6 "
-                    "uniform) x mean candidates per round of this run",
-                    "alg_bytes_per_launch": bytes_k[dom] / max(totals["n_profiled"] / args.steps, 1),
-                    "share_of_step": per_step_ms / ms,
-                    "kernel_ms_per_step": {k: v / args.steps for k, v in times_k.items()},
-                    "launches_per_step": totals["n_profiled"] / args.steps,
-                    "alg_bytes_per_step": bytes_k[dom]}
+    cfb = {"C": None, "F": None}
+    if not args.no_profile:
+        prof = profiled(xd, 2, stream, max_walk_steps=args.max_walk, schedule=sched) if params is None else None
+        if prof is not None:
+            roofline, cfb = roofline_of(prof, 2, ms, peak, peak_kind)
     line = {
         "metric": METRIC, "value": value, "unit": "Mtets/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -652,16 +773,20 @@ def main():
                    "tets": ntet, "l2": "inputs and tetrahedron store larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "baseline_ref": "paper Fig. 9, AMD EPYC 7551, 1e7 uniform: 31.3 Mtets/s",
+                   "engine": "asynchronous (lock-based per-warp segments) + round-based hand-offs",
                    "stats": {k: stat_acc[k] for k in ("n_rounds", "n_passes", "n_attempts",
                                                       "n_conflicts", "n_big", "n_exact", "n_sos",
                                                       "sum_walk", "max_walk", "n_walk_limit",
                                                       "n_rounds_wave", "n_rounds_retry", "n_rounds_big",
-                                                      "ms_first_round")},
+                                                      "ms_first_round", "n_async", "n_restarts",
+                                                      "n_exact_handoff", "n_inserted_async")},
                    "mean_C": cfb["C"], "mean_F": cfb["F"],
                    "exact_per_point": stat_acc["n_exact"] / max(stat_acc["n_unique"], 1),
                    "perturbed_per_point": stat_acc["n_sos"] / max(stat_acc["n_unique"], 1),
                    "retry_passes": stat_acc["n_passes"],
-                   "ms_sort": stat_acc["ms_sort"], "ms_insert": stat_acc["ms_insert"]},
+                   "ms_sort": stat_acc["ms_sort"], "ms_insert": stat_acc["ms_insert"],
+                   "device_bytes_per_point": stat_acc["device_bytes"] / n,
+                   "bit_exact_full": bit_exact_full, "digest_of": name},
         "e2e": {"value": e2e_value, "unit": "Mtets/s", "h2d_bytes_per_step": n * 24,
                 "d2h_bytes_per_step": T * 16, "ms": statistics.median(e2e_ms)},
         "gpu_launches": launches,
@@ -671,9 +796,13 @@ def main():
     if learned_info is not None:
         learned_info["learned_over_plain"] = value / learned_info["plain"]["value"]
         line["learned"] = learned_info
+    tri.close()
+    del xd
+    torch.cuda.empty_cache()
     if world == 1 and not args.no_extras and args.kind == "uniform" and args.schedule == "plain":
         # the other rows of the hot path on the same GPU in the same run: the batched form against
-        # one plain launch sequence per cloud, and the learned schedule against the plain one
+        # one plain launch sequence per cloud, the 1e8 scale, the learned schedule against the
+        # plain one on the 1e8 cube + slab, and Delaunay refinement of a box
         import argparse as _ap
         bargs = _ap.Namespace(clouds=args.clouds, steps=3, warmup=2, e2e_steps=0, plain_sample=32,
                               no_cpu_baseline=True)
@@ -684,13 +813,13 @@ def main():
                          "batched_over_plain": bl["batched_over_plain"], "roofline_frac": bl["roofline"]["frac"],
                          "shape": [bl["config"]["batch_warps"], bl["config"]["batch_min_blocks"],
                                    bl["config"]["batch_alpha"]], "graph_replay": bl["config"]["graph_replay"]}
-        line["learned"], _ = learned_vs_plain(1e7, 3, 1, args.train_steps)
+        line["scale_1e8"] = scale_run("uniform", 1e8, SEED, 2, 1)
+        line["learned"], _ = learned_vs_plain(1e8, 2, 1, args.train_steps, seed=5)
         line["refine"] = refine_run(REFINE_K, 3, 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["cpu_paper_scheme"] = cpu_baseline(x_host, args.cpu_sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tri.close()
     if dist is not None:
         dist.destroy_process_group()
 

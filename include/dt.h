@@ -106,6 +106,15 @@ typedef struct {
   double ms_batch_tune;    /* dt_batch: host time of the autotuning in the last call (0 = reused) */
   uint64_t batch_graph;    /* dt_batch: 1 if the last call replayed its captured CUDA graph */
   uint64_t batch_min_blocks; /* dt_batch: resident blocks per SM the chosen shape was built for */
+  double ms_async;         /* summed device time of the asynchronous insertion launches
+                              (DT_FLAG_PROFILE only) */
+  uint64_t n_async;        /* asynchronous insertion launches (one per wave or retry pass) */
+  uint64_t n_restarts;     /* asynchronous insertions that found their cavity changed under the
+                              locks and started over */
+  uint64_t device_bytes;   /* device memory the handle holds */
+  uint64_t n_exact_handoff; /* points the asynchronous engine handed to the round-based engine
+                               because its FP32 predicate stage could not decide a test */
+  uint64_t n_inserted_async; /* insertions made by the asynchronous engine */
   uint64_t reserved[2];
 } dt_stats;
 

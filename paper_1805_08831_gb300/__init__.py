@@ -58,6 +58,9 @@ class Stats(ctypes.Structure):
                    ("n_clouds_degenerate", ctypes.c_uint64), ("batch_warps", ctypes.c_uint64),
                    ("batch_alpha", ctypes.c_double), ("ms_batch_tune", ctypes.c_double),
                    ("batch_graph", ctypes.c_uint64), ("batch_min_blocks", ctypes.c_uint64),
+                   ("ms_async", ctypes.c_double), ("n_async", ctypes.c_uint64),
+                   ("n_restarts", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                   ("n_exact_handoff", ctypes.c_uint64), ("n_inserted_async", ctypes.c_uint64),
                    ("reserved", ctypes.c_uint64 * 2)])
 
     def as_dict(self):
@@ -66,7 +69,7 @@ class Stats(ctypes.Structure):
                   "n_profiled", "device_error", "device_error_info", "n_rounds_wave",
                   "n_rounds_retry", "n_rounds_big", "ms_first_round", "n_walk_limit", "free_slots",
                   "max_walk", "n_clouds_degenerate", "batch_warps", "batch_alpha", "ms_batch_tune",
-                  "batch_graph", "batch_min_blocks"):
+                  "batch_graph", "batch_min_blocks", "ms_async", "n_async", "n_restarts", "device_bytes", "n_exact_handoff", "n_inserted_async"):
             d[f] = getattr(self, f)
         return d
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdt_gb300.so")
 RUNNER = os.path.join(BUILD, "dt_run")
-SOURCES = ["order.cu", "dt.cu", "batch.cu", "mlp.cu", "refine.cu"]
+SOURCES = ["order.cu", "dt.cu", "async.cu", "batch.cu", "mlp.cu", "refine.cu"]
 HEADERS = ["common.cuh", "predicates.cuh", "engine.cuh", "internal.h"]
 
 NVCC_FLAGS = [

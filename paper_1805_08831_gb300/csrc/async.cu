@@ -1,0 +1,787 @@
+// Asynchronous concurrent insertion: one persistent launch per wave, no rounds.
+//
+// The paper's threads (Section 3.2) each own a Moore-curve partition of the points and insert
+// them one after the other; a thread that would touch a tetrahedron another thread holds aborts
+// the insertion and retries it later. Here every warp is such a thread: warp w takes the w-th
+// contiguous segment of the wave's Moore order and inserts its points in that order, each walk
+// starting from the warp's previous ball (Algorithm 1). Ownership is a 32-bit word per
+// tetrahedron slot (0 = free, else the owning warp). One insertion:
+//   1. walk (Section 2.1) from the previous ball, reading the mesh without locks;
+//   2. cavity search (Section 2.1, Eq. 1) on those unlocked reads: the cavity C, its outside
+//      neighbours A and the boundary facets, with every record kept in shared memory;
+//   3. lock C, A and the slots the ball needs beyond C (Section 2.5 reuses C's slots first),
+//      one compare-and-swap each; any slot held by another warp aborts the insertion (rule
+//      (1) of Section 3.2: a thread touches only tetrahedra it owns);
+//   4. re-read C (whole records) and A (vertices) under the locks: a difference means another
+//      warp changed them between steps 2 and 3, and the insertion starts over from the walk;
+//   5. write the ball (Section 2.5: one tetrahedron per boundary facet, adjacency through the
+//      edge table), the back-pointers of A, then release every lock after a fence.
+// Aborted points wait in a small per-warp list and are retried after later insertions; what is
+// still left when the segment ends goes to the next pass. Cavities larger than the per-warp
+// workspace go to the large-cavity rounds. No warp ever waits on another, so every loop here
+// is bounded by the segment length and fixed retry counts.
+//
+// The triangulation does not depend on the order of insertions (exact predicates and one
+// symbolic perturbation, Section 2.4), so this engine gives the same tetrahedra as the
+// round-based one.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "common.cuh"
+#include "engine.cuh"
+#include "internal.h"
+#include "predicates.cuh"
+
+namespace dtg {
+namespace {
+
+constexpr int kAW = 4;            // warps per block
+constexpr int kAHash = 256;       // visited-set slots per warp
+constexpr int kACMax = 64;        // cavity tetrahedra
+constexpr int kAAMax = 64;        // outside tetrahedra (+ verify-only records)
+constexpr int kAFMax = 60;        // boundary facets (<= 32 boundary vertices: the 32 x 32 edge table)
+constexpr int kAPool = 96;        // private free slots
+constexpr int kADefer = 16;       // aborted points waiting for a retry
+constexpr int kARetry = 3;        // immediate restarts after a failed re-read
+constexpr uint32_t kAChunk = 32;  // slots taken from the allocator at a time
+constexpr uint32_t kVerifyOnly = 0x80000000u;  // outside-list entry read but not locked
+
+enum AStatus : int { kAInserted = 0, kALost = 1, kARestart = 2, kABig = 3, kAWalkLimit = 4, kADup = 5, kAExact = 6 };
+
+// Shared-memory workspace of one warp. The visited set is needed only while the cavity is
+// searched, the edge table only while the ball is built: they share their bytes.
+struct AsyncWS {
+  uint32_t cl[kACMax];       // cavity slots
+  Tet cr[kACMax];            // their records as read
+  uint32_t al[kAAMax];       // outside slots (kVerifyOnly: read for a ghost test, not locked)
+  uint4 av[kAAMax];          // their vertex ids as read
+  uint32_t slot[kAFMax];     // slots of the new tetrahedra
+  uint32_t ex[kAFMax];       // slots beyond the cavity's, taken from the pool
+  uint32_t vkey[32];
+  uint32_t pool[kAPool];
+  uint32_t defer[kADefer];
+  uint8_t bl_ci[kAFMax];     // boundary facet: cavity index
+  uint8_t bl_f[kAFMax];      // boundary facet: facet
+  // the warp's state, uniform across its lanes (written by lane 0)
+  unsigned long long fa, bump;  // allocator snapshot of the launch
+  unsigned int cnt[8];          // inserted, lost, attempts, sum |C|, sum |B|, walk steps, restarts
+  uint32_t hint;                // the warp's last ball
+  int np;                       // slots in the pool
+  int nc, na, nb;               // cavity, outside and boundary-facet counts of the last search
+  union {
+    struct {
+      uint32_t hkey[kAHash];
+      uint8_t hval[kAHash];
+    };
+    uint16_t tab[32 * 32];
+  };
+};
+
+__device__ __forceinline__ Tet ld_tet(const Tet* T, uint32_t t) { return load_tet_cg(T, t); }
+
+__device__ __forceinline__ bool same_tet(const Tet& a, const Tet& b) {
+  return a.v.x == b.v.x && a.v.y == b.v.y && a.v.z == b.v.z && a.v.w == b.v.w && a.n.x == b.n.x &&
+         a.n.y == b.n.y && a.n.z == b.n.z && a.n.w == b.n.w;
+}
+
+__device__ __forceinline__ bool same_v(const uint4& a, const uint4& b) {
+  return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
+}
+
+// A record that references only allocated vertices and slots (a record being rewritten may be
+// read half old, half new; such a read is never followed).
+__device__ __forceinline__ bool rec_ok(const Tet& T, uint32_t ntets, uint32_t npts) {
+  bool ok = true;
+  for (int k = 0; k < 4; ++k) {
+    uint32_t v = get4(T.v, k), n = get4(T.n, k);
+    ok = ok && (v == kGhost || v < npts) && (n >> 2) < ntets;
+  }
+  return ok;
+}
+
+// The predicates' FP32 stage on the double-float point copy (predicates.cuh: rigorous error
+// bounds, Section 2.4's filters moved to FP32). When it cannot decide, the insertion is handed to
+// the round-based engine, which runs the whole cascade (FP64 filter, exact arithmetic, symbolic
+// perturbation): keeping the exact stages out of this kernel keeps its registers free of the
+// save and restore traffic their calls would cost. A return of 0 means "undecided".
+
+// orient3d of (v0, v1, v2, v3) with vertex i replaced by p.
+__device__ __forceinline__ int orient_with_p(const Ctx& c, int i, const PtF& FP, const PtF& F0, const PtF& F1,
+                                             const PtF& F2, const PtF& F3) {
+  switch (i) {
+    case 0: return orient3d_f(FP, F1, F2, F3, c.eta);
+    case 1: return orient3d_f(F0, FP, F2, F3, c.eta);
+    case 2: return orient3d_f(F0, F1, FP, F3, c.eta);
+    default: return orient3d_f(F0, F1, F2, FP, c.eta);
+  }
+}
+
+// Insphere of a finite tetrahedron v and p: -1 inside, 1 outside, 0 undecided.
+__device__ __forceinline__ int inside_async(const Ctx& c, const uint4& v, const PtF& FP) {
+  PtF A = load_ptf(c.ptf, v.x), B = load_ptf(c.ptf, v.y), C = load_ptf(c.ptf, v.z), D = load_ptf(c.ptf, v.w);
+  return insphere_f(A, B, C, D, FP, c.eta);
+}
+
+// Visibility walk (Section 2.1, ghost rules of Section 2.6) on unlocked reads, by one lane. A
+// record that is being rewritten may be read half old, half new: such reads end the walk with
+// kARestart (or it runs into its step bound); nothing is trusted before step 4 re-reads it
+// under a lock.
+__device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& FP, uint32_t start, uint32_t salt,
+                                          uint32_t max_steps, uint32_t* t_out, uint32_t* steps_out) {
+  uint32_t t = start;
+  Tet T;
+  int hops = 0;
+  *steps_out = 0;
+  for (;;) {
+    if (t == kNone || t >= c.ntets) t = __ldcg(&c.st->anchor);
+    if (t >= c.ntets) return kARestart;
+    T = ld_tet(c.tets, t);
+    if (!tet_dead(T.v)) break;
+    t = T.n.x;  // dead slot: follow its redirect
+    if (++hops > 64) return kARestart;
+  }
+  if (!rec_ok(T, c.ntets, c.npts)) return kARestart;
+  int g = ghost_pos(T.v);
+  if (g >= 0) {
+    t = get4(T.n, g) >> 2;
+    T = ld_tet(c.tets, t);
+    if (tet_dead(T.v) || !rec_ok(T, c.ntets, c.npts)) return kARestart;
+  }
+  uint32_t prev = kNone, steps = 0;
+  for (;;) {
+    if (ghost_pos(T.v) >= 0) break;
+    const PtF F0 = load_ptf(c.ptf, T.v.x), F1 = load_ptf(c.ptf, T.v.y), F2 = load_ptf(c.ptf, T.v.z),
+              F3 = load_ptf(c.ptf, T.v.w);
+    int exit = -1;
+    const int s0 = (salt + steps) & 3;
+    for (int k = 0; k < 4; ++k) {
+      const int i = (s0 + k) & 3;
+      if ((get4(T.n, i) >> 2) == prev) continue;
+      const int o = orient_with_p(c, i, FP, F0, F1, F2, F3);
+      if (o == 0) return kAExact;
+      if (o < 0) {
+        exit = i;
+        break;
+      }
+    }
+    if (exit < 0) {
+      bool dup = false;
+      if (same_f(F0, FP) || same_f(F1, FP) || same_f(F2, FP) || same_f(F3, FP)) {
+        Pt P = load_pt(c.pts, p);
+        for (int k = 0; k < 4; ++k) {
+          Pt V = load_pt(c.pts, get4(T.v, k));
+          dup = dup || (V.x == P.x && V.y == P.y && V.z == P.z);
+        }
+      }
+      *t_out = t;
+      *steps_out = steps;
+      return dup ? kADup : kAInserted;
+    }
+    if (steps >= max_steps) {
+      *t_out = t;
+      *steps_out = steps;
+      return kAWalkLimit;
+    }
+    prev = t;
+    t = get4(T.n, exit) >> 2;
+    T = ld_tet(c.tets, t);
+    ++steps;
+    if (tet_dead(T.v) || !rec_ok(T, c.ntets, c.npts)) {
+      *t_out = t;
+      *steps_out = steps;
+      return kARestart;
+    }
+  }
+  *t_out = t;
+  *steps_out = steps;
+  return kAInserted;
+}
+
+// Conflict of a record U (already read) with p: 1 in the cavity, 0 outside, -1 the record (or
+// the one a ghost test needs) is inconsistent, -2 undecided by the FP32 stage. For a ghost whose
+// hull facet's plane holds p, the finite neighbour across the facet decides (Section 2.6); its
+// slot and vertices go to *r / *rv.
+__device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const PtF& FP, uint32_t* r, uint4* rv) {
+  const int g = ghost_pos(U.v);
+  if (g < 0) {
+    const int s = inside_async(c, U.v, FP);
+    return s < 0 ? 1 : (s > 0 ? 0 : -2);
+  }
+  int o;
+  switch (g) {  // orientation of the hull facet's three vertices and p in the ghost's place
+    case 0: o = orient3d_f(FP, load_ptf(c.ptf, U.v.y), load_ptf(c.ptf, U.v.z), load_ptf(c.ptf, U.v.w), c.eta); break;
+    case 1: o = orient3d_f(load_ptf(c.ptf, U.v.x), FP, load_ptf(c.ptf, U.v.z), load_ptf(c.ptf, U.v.w), c.eta); break;
+    case 2: o = orient3d_f(load_ptf(c.ptf, U.v.x), load_ptf(c.ptf, U.v.y), FP, load_ptf(c.ptf, U.v.w), c.eta); break;
+    default: o = orient3d_f(load_ptf(c.ptf, U.v.x), load_ptf(c.ptf, U.v.y), load_ptf(c.ptf, U.v.z), FP, c.eta); break;
+  }
+  if (o != 0) return o > 0 ? 1 : 0;
+  // p on the facet's plane as far as the FP32 stage can tell: the exact rule needs the
+  // round-based engine (the plane test and the neighbour's perturbed sphere)
+  (void)r;
+  (void)rv;
+  return -2;
+}
+
+__device__ __forceinline__ int hfind(const AsyncWS& w, uint32_t key) {
+  uint32_t h = (hash32(key) >> 8) & (kAHash - 1);
+  for (int probe = 0; probe < kAHash; ++probe) {
+    uint32_t k = vld(&w.hkey[h]);
+    if (k == key) return vld(&w.hval[h]);
+    if (k == kNone) return 0;
+    h = (h + 1) & (kAHash - 1);
+  }
+  return 0;
+}
+
+__device__ __forceinline__ bool hinsert(AsyncWS& w, uint32_t key, uint8_t val) {
+  uint32_t h = (hash32(key) >> 8) & (kAHash - 1);
+  for (int probe = 0; probe < kAHash; ++probe) {
+    uint32_t old = atomicCAS(&w.hkey[h], kNone, key);
+    if (old == kNone || old == key) {
+      w.hval[h] = val;
+      return true;
+    }
+    h = (h + 1) & (kAHash - 1);
+  }
+  return false;
+}
+
+// Step 2: the cavity of p from t0 on unlocked reads. Returns kAInserted (lists filled),
+// kARestart (an inconsistent read) or kABig (the workspace is too small).
+__device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t0, uint32_t p, const PtF& FP) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < kAHash; i += 32) w.hkey[i] = kNone;
+  __syncwarp();
+  int flag = 0;  // 1 restart, 2 big, 4 a predicate the FP32 stage cannot decide
+  if (lane == 0) {
+    const Tet T = ld_tet(c.tets, t0);
+    uint32_t r = kNone;
+    uint4 rv{};
+    const int in = (tet_dead(T.v) || !rec_ok(T, c.ntets, c.npts)) ? -1 : conflict_async(c, T, FP, &r, &rv);
+    int na = 0;
+    if (in == -2) {
+      flag = 4;
+    } else if (in != 1) {
+      flag = 1;
+    } else {
+      w.cl[0] = t0;
+      w.cr[0] = T;
+      hinsert(w, t0, 1);
+      if (r != kNone) {
+        w.al[0] = r | kVerifyOnly;
+        w.av[0] = rv;
+        na = 1;
+      }
+    }
+    w.nc = 1;
+    w.na = na;
+    w.nb = 0;
+  }
+  flag = __shfl_sync(kFull, flag, 0);
+  __syncwarp();
+  if (flag & 4) return kAExact;
+  if (flag) return kARestart;
+  int nc = 1, na = w.na, nb = 0, head = 0;
+  while (head < nc && flag == 0) {
+    const int batch = min(8, nc - head);
+    const int k = lane >> 2, f = lane & 3;
+    bool active = k < batch;
+    const int ci = head + k;
+    uint32_t u = kNone;
+    if (active) {
+      u = get4(w.cr[ci].n, f) >> 2;
+      if (u >= c.ntets) {
+        flag = 1;
+        active = false;
+      }
+    }
+    flag = __reduce_or_sync(kFull, flag);
+    if (flag) break;
+    head += batch;
+    const int known = active ? hfind(w, u) : 0;
+    const bool need = active && known == 0;
+    const unsigned peers = __match_any_sync(kFull, need ? u : 0xFFFFFFFFu);
+    const int leader = __ffs(peers) - 1;
+    const bool is_leader = need && lane == leader;
+    int res = 0, myflag = 0;
+    uint32_t r = kNone;
+    uint4 rv{};
+    Tet U;
+    if (is_leader) {
+      U = ld_tet(c.tets, u);
+      const int in = (tet_dead(U.v) || !rec_ok(U, c.ntets, c.npts)) ? -1 : conflict_async(c, U, FP, &r, &rv);
+      if (in == -2) {
+        myflag |= 4;
+      } else if (in < 0) {
+        myflag |= 1;
+      } else {
+        res = in ? 1 : 2;
+        if (!hinsert(w, u, (uint8_t)res)) myflag |= 2;
+      }
+    }
+    const int lres = __shfl_sync(kFull, res, leader);
+    res = need ? lres : known;
+    const bool addC = is_leader && res == 1;
+    const unsigned mC = __ballot_sync(kFull, addC);
+    if (addC) {
+      const int pos = nc + __popc(mC & lanemask_lt());
+      if (pos < kACMax) {
+        w.cl[pos] = u;
+        w.cr[pos] = U;
+      }
+    }
+    nc += __popc(mC);
+    // outside tetrahedra (locked) and the finite neighbours ghost tests read (verify only)
+    const bool addA = is_leader && res == 2;
+    const bool addR = is_leader && r != kNone;
+    const unsigned mA = __ballot_sync(kFull, addA), mR = __ballot_sync(kFull, addR);
+    if (addA) {
+      const int pos = na + __popc(mA & lanemask_lt());
+      if (pos < kAAMax) {
+        w.al[pos] = u;
+        w.av[pos] = U.v;
+      }
+    }
+    na += __popc(mA);
+    if (addR) {
+      const int pos = na + __popc(mR & lanemask_lt());
+      if (pos < kAAMax) {
+        w.al[pos] = r | kVerifyOnly;
+        w.av[pos] = rv;
+      }
+    }
+    na += __popc(mR);
+    const bool addB = active && res == 2;
+    const unsigned mB = __ballot_sync(kFull, addB);
+    if (addB) {
+      const int pos = nb + __popc(mB & lanemask_lt());
+      if (pos < kAFMax) {
+        w.bl_ci[pos] = (uint8_t)ci;
+        w.bl_f[pos] = (uint8_t)f;
+      }
+    }
+    nb += __popc(mB);
+    flag = __reduce_or_sync(kFull, myflag);
+    if (nc > kACMax || na > kAAMax || nb > kAFMax) flag |= 2;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    w.nc = nc;
+    w.na = na;
+    w.nb = nb;
+  }
+  __syncwarp();
+  if (flag & 4) return kAExact;
+  if (flag & 1) return kARestart;
+  if (flag & 2) return kABig;
+  return kAInserted;
+}
+
+// Slot of lock-list entry i: cavity slots, then the outside slots that are locked, then the
+// ball's extra slots. Verify-only outside entries give kNone (not locked).
+__device__ __forceinline__ uint32_t lock_entry(const AsyncWS& w, int i, int nc, int na, int nx) {
+  if (i < nc) return w.cl[i];
+  i -= nc;
+  if (i < na) {
+    const uint32_t a = w.al[i];
+    return (a & kVerifyOnly) ? kNone : a;
+  }
+  i -= na;
+  return i < nx ? w.ex[i] : kNone;
+}
+
+// Releases the locks of the entries this lane took (bit k of `held` = entry lane + 32 k).
+__device__ __forceinline__ void release_held(const AsyncWS& w, uint32_t* lock, unsigned held, int nc, int na, int nx) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; held; ++k, held >>= 1)
+    if (held & 1u) __stcg(&lock[lock_entry(w, lane + 32 * k, nc, na, nx)], 0u);
+}
+
+// Takes n slots from the warp's pool into w.ex, refilling it from the allocator (free list,
+// then the bump pointer, as in the round-based engine). False when the store is full.
+__device__ __forceinline__ bool pool_take(const Ctx& c, AsyncWS& w, int n) {
+  const int lane = threadIdx.x & 31;
+  int np = w.np;
+  while (np < n) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&c.st->alloc_cursor, (unsigned long long)kAChunk);
+    base = __shfl_sync(kFull, base, 0);
+    bool fail = false;
+    const uint32_t s = virtual_slot(c, base + lane, w.fa, w.bump, c.st->capacity, fail);
+    if (__any_sync(kFull, fail)) {
+      if (lane == 0) raise_error(c.st, kErrCapacity, 0xA5u);
+      return false;
+    }
+    w.pool[np + lane] = s;  // np < n <= kAFMax, so np + 32 <= kAPool
+    np += 32;
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) w.ex[i] = w.pool[np - 1 - i];
+  __syncwarp();
+  if (lane == 0) w.np = np - n;
+  __syncwarp();
+  return true;
+}
+
+// Puts n slots s[0, n) back into the pool; what does not fit goes to the pending list.
+__device__ __forceinline__ void pool_give(const Ctx& c, AsyncWS& w, const uint32_t* s, int n) {
+  const int lane = threadIdx.x & 31;
+  const int np = w.np;
+  const int keep = min(n, kAPool - np);
+  for (int i = lane; i < keep; i += 32) w.pool[np + i] = s[i];
+  if (n > keep) {
+    unsigned long long pb = 0;
+    if (lane == 0) pb = atomicAdd(&c.st->pending, (unsigned long long)(n - keep));
+    pb = __shfl_sync(kFull, pb, 0);
+    for (int i = keep + lane; i < n; i += 32) {
+      if (pb + (i - keep) < c.st->free_capacity) c.pending[pb + (i - keep)] = s[i];
+      else raise_error(c.st, kErrFreeList, 0xA7u);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) w.np = np + keep;
+  __syncwarp();
+}
+
+// One attempt at inserting p (steps 1-5). w.hint is the warp's last ball, updated on success.
+__device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lock, uint32_t me, uint32_t p,
+                                          const InsertLog& lg) {
+  const int lane = threadIdx.x & 31;
+  const PtF FP = load_ptf(c.ptf, p);
+  for (int attempt = 0; attempt <= kARetry; ++attempt) {
+    // 1. walk (one lane)
+    int ws = 0;
+    uint32_t t0 = kNone;
+    if (lane == 0) {
+      uint32_t start = attempt == 0 ? w.hint : c.point_hint[p];
+      if (start == kNone) start = c.point_hint[p];
+      if (start == kNone) {
+        uint32_t f, g;
+        cells_of(c, FP, &f, &g);
+        start = c.cell_hint[f];
+        if (start == kNone) start = c.cell_hint2[g];
+      }
+      uint32_t steps = 0;
+      ws = walk_async(c, p, FP, start, p * 0x9E3779B1u >> 30, c.max_walk, &t0, &steps);
+      if (t0 != kNone && t0 < c.ntets) c.point_hint[p] = t0;
+      w.cnt[5] += steps;
+    }
+    ws = __shfl_sync(kFull, ws, 0);
+    t0 = __shfl_sync(kFull, t0, 0);
+    if (ws == kADup || ws == kAWalkLimit || ws == kAExact) return ws;
+    if (ws == kARestart) {
+      if (lane == 0) w.cnt[6] += 1;
+      continue;
+    }
+    // 2. cavity on unlocked reads
+    const int r = cavity_async(c, w, t0, p, FP);
+    if (r == kABig || r == kAExact) return r;
+    if (r == kARestart) {
+      if (lane == 0) w.cnt[6] += 1;
+      continue;
+    }
+    const int nc = w.nc, na = w.na, nb = w.nb;
+    const int reuse = min(nc, nb), nx = nb - reuse;
+    if (nx > 0 && !pool_take(c, w, nx)) return kALost;
+    // 3. lock C, A and the extra slots
+    const int nl = nc + na + nx;
+    unsigned held = 0;
+    bool ok = true;
+    for (int k = 0; lane + 32 * k < nl; ++k) {
+      const uint32_t s = lock_entry(w, lane + 32 * k, nc, na, nx);
+      if (s == kNone) continue;
+      if (atomicCAS(&lock[s], 0u, me) == 0u) held |= 1u << k;
+      else ok = false;
+    }
+    if (!__all_sync(kFull, ok)) {
+      release_held(w, lock, held, nc, na, nx);
+      if (nx > 0) pool_give(c, w, w.ex, nx);
+      return kALost;
+    }
+    __threadfence();
+    // 4. re-read under the locks
+    bool same = true;
+    for (int i = lane; i < nc; i += 32) same = same && same_tet(ld_tet(c.tets, w.cl[i]), w.cr[i]);
+    for (int i = lane; i < na; i += 32) {
+      const uint32_t a = w.al[i] & ~kVerifyOnly;
+      same = same && same_v(__ldcg(reinterpret_cast<const uint4*>(c.tets + a)), w.av[i]);
+    }
+    if (!__all_sync(kFull, same)) {
+      release_held(w, lock, held, nc, na, nx);
+      if (nx > 0) pool_give(c, w, w.ex, nx);
+      if (lane == 0) w.cnt[6] += 1;
+      continue;
+    }
+    // 5. the ball: cavity slots first, then the extra slots
+    for (int i = lane; i < nb; i += 32) w.slot[i] = i < reuse ? w.cl[i] : w.ex[i - reuse];
+    w.vkey[lane] = kNoVertex;
+    __syncwarp();
+    bool vfail = false;
+    for (int i = lane; i < nb; i += 32) {
+      const int ci = w.bl_ci[i], f = w.bl_f[i];
+      uint4 v = w.cr[ci].v;
+      set4(v, f, p);
+      int a, b, cc;
+      after_pos(f, a, b, cc);
+      const int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
+      if (la < 0 || lb < 0 || lc < 0) {
+        vfail = true;
+        continue;
+      }
+      w.tab[lb * 32 + lc] = (uint16_t)((i << 2) | a);
+      w.tab[lc * 32 + la] = (uint16_t)((i << 2) | b);
+      w.tab[la * 32 + lb] = (uint16_t)((i << 2) | cc);
+    }
+    __syncwarp();
+    // every internal facet was recorded by its two sides (the cavity was verified under the
+    // locks, so its boundary is a closed surface); a lookup that finds no partner is a bug
+    bool bad = __any_sync(kFull, vfail);
+    for (int i = lane; i < nb && !bad; i += 32) {
+      const int ci = w.bl_ci[i], f = w.bl_f[i];
+      uint4 v = w.cr[ci].v;
+      const uint32_t out = get4(w.cr[ci].n, f);
+      set4(v, f, p);
+      int a, b, cc;
+      after_pos(f, a, b, cc);
+      const int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
+      const uint32_t ea = vld(&w.tab[lc * 32 + lb]), eb = vld(&w.tab[la * 32 + lc]), ec = vld(&w.tab[lb * 32 + la]);
+      if ((ea >> 2) >= (uint32_t)nb || (eb >> 2) >= (uint32_t)nb || (ec >> 2) >= (uint32_t)nb ||
+          (ea >> 2) == (uint32_t)i || (eb >> 2) == (uint32_t)i || (ec >> 2) == (uint32_t)i) {
+        bad = true;
+        break;
+      }
+      uint4 n4;
+      set4(n4, f, out);
+      set4(n4, a, 4u * w.slot[ea >> 2] + (ea & 3u));
+      set4(n4, b, 4u * w.slot[eb >> 2] + (eb & 3u));
+      set4(n4, cc, 4u * w.slot[ec >> 2] + (ec & 3u));
+      const uint32_t s = w.slot[i];
+      uint4* dst = reinterpret_cast<uint4*>(c.tets + s);
+      __stcg(dst, v);
+      __stcg(dst + 1, n4);
+      __stcg(reinterpret_cast<uint32_t*>(&c.tets[out >> 2].n) + (out & 3u), 4u * s + (uint32_t)f);
+    }
+    if (__any_sync(kFull, bad)) {
+      if (lane == 0) raise_error(c.st, kErrInternal, 0xA8u);
+      release_held(w, lock, held, nc, na, nx);
+      return kALost;
+    }
+    // cavity slots left over (|C| > |B|) die, keep a redirect into the ball, and join the pool
+    const int freed = nc - nb;
+    if (freed > 0) {
+      const uint32_t redirect = w.slot[0];
+      for (int i = lane; i < freed; i += 32) {
+        uint4* dst = reinterpret_cast<uint4*>(c.tets + w.cl[nb + i]);
+        __stcg(dst, make_uint4(kDeadMark, kDeadMark, kDeadMark, kDeadMark));
+        __stcg(dst + 1, make_uint4(redirect, kNone, kNone, kNone));
+      }
+    }
+    __threadfence();
+    release_held(w, lock, held, nc, na, nx);
+    if (freed > 0) pool_give(c, w, w.cl + nb, freed);
+    if (lane == 0) {
+      const uint32_t s0 = w.slot[0];
+      uint32_t f, g;
+      cells_of(c, FP, &f, &g);
+      c.cell_hint[f] = s0;
+      c.cell_hint2[g] = s0;
+      c.point_hint[p] = s0;
+      // the handle's state shares one cache line with the allocator's atomics: every warp
+      // writing it per insertion serialised the whole launch, so it is refreshed now and then
+      if ((w.cnt[0] & 63u) == 0) c.st->anchor = s0;
+      log_outcome(lg, p, kCandInserted, nc);
+      w.hint = s0;
+      w.cnt[0] += 1;
+      w.cnt[3] += nc;
+      w.cnt[4] += nb;
+    }
+    __syncwarp();
+    return kAInserted;
+  }
+  return kALost;
+}
+
+// Hands point p to a queue of the host's next step (0: next pass, 1: large cavities, 2: the
+// round-based engine's exact predicates). Lane 0.
+__device__ __forceinline__ void to_queue(const AsyncIO& io, const Ctx& c, int q, uint32_t p) {
+  uint32_t* out = q == 0 ? io.lose_out : (q == 1 ? io.big_out : io.exact_out);
+  const int qi = q == 0 ? io.lose_q : (q == 1 ? io.big_q : io.exact_q);
+  const unsigned long long b = atomicAdd(&c.st->q[qi], 1ull);
+  out[b] = p;
+}
+
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO io, uint32_t* lock,
+                                                               const uint8_t* __restrict__ vflag, InsertLog lg) {
+  __shared__ AsyncWS s_ws[kAW];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  AsyncWS& w = s_ws[wid];
+  const uint32_t seg = blockIdx.x * kAW + wid;
+  if (seg >= io.W) return;
+  const uint32_t me = seg + 1;
+  const uint64_t b0 = (uint64_t)seg * io.L;
+  const uint64_t e0 = b0 + io.L < io.m ? b0 + io.L : io.m;
+  if (lane == 0) {
+    w.fa = __ldcg(&c.st->free_avail);
+    w.bump = __ldcg(&c.st->bump);
+    w.np = 0;
+    for (int k = 0; k < 8; ++k) w.cnt[k] = 0;
+    w.hint = b0 < e0 ? c.point_hint[io.q ? io.q[b0] : io.qbase + (uint32_t)b0] : kNone;
+  }
+  __syncwarp();
+  int nd = 0, dhead = 0;
+  uint64_t i = b0;
+  int since = 0;  // insertions since the last retry of a deferred point
+  for (;;) {
+    __syncwarp();  // lane 0's writes to the deferred list are seen by every lane below
+    uint32_t p;
+    bool retried = false;
+    if (nd > 0 && (i >= e0 || since >= 4)) {
+      p = w.defer[dhead];
+      dhead = (dhead + 1) % kADefer;
+      --nd;
+      retried = true;
+      since = 0;
+    } else if (i < e0) {
+      p = io.q ? io.q[i] : io.qbase + (uint32_t)i;
+      ++i;
+      if (vflag[p] != 0) continue;
+    } else {
+      break;
+    }
+    if (lane == 0) w.cnt[2] += 1;
+    const int r = try_insert(c, w, lock, me, p, lg);
+    // a raised error stops the launch; read every 16 points for the same reason as the anchor
+    unsigned err = 0;
+    if (lane == 0 && (w.cnt[2] & 15u) == 0) err = __ldcg(&c.st->error);
+    if (__shfl_sync(kFull, err, 0) != 0u) break;
+    if (r == kAInserted) {
+      ++since;
+      continue;
+    }
+    // every lane holds the same r, nd, dhead and `retried`: the decisions below are uniform
+    if (r == kALost && lane == 0) {
+      w.cnt[1] += 1;
+      log_outcome(lg, p, kCandLost, 0);
+    }
+    if (r == kADup) {
+      if (lane == 0) atomicAdd(&c.st->n_dups, 1ull);
+    } else if (r == kABig) {
+      if (lane == 0) to_queue(io, c, 1, p);
+    } else if (r == kAExact) {
+      if (lane == 0) to_queue(io, c, 2, p);
+    } else if (r == kALost && !retried && nd < kADefer) {
+      if (lane == 0) w.defer[(dhead + nd) % kADefer] = p;
+      ++nd;
+    } else {  // a walk over its step bound, or a point that lost again: the next pass
+      if (lane == 0) to_queue(io, c, 0, p);
+    }
+  }
+  __syncwarp();
+  // what is left: deferred points to the next pass, unused slots back to the allocator
+  if (lane == 0)
+    for (int k = 0; k < nd; ++k) to_queue(io, c, 0, w.defer[(dhead + k) % kADefer]);
+  const int np = w.np;
+  if (np > 0) {
+    unsigned long long pb = 0;
+    if (lane == 0) pb = atomicAdd(&c.st->pending, (unsigned long long)np);
+    pb = __shfl_sync(kFull, pb, 0);
+    for (int k = lane; k < np; k += 32) {
+      if (pb + k < c.st->free_capacity) c.pending[pb + k] = w.pool[k];
+      else raise_error(c.st, kErrFreeList, 0xA9u);
+    }
+  }
+  if (lane == 0) {
+    unsigned long long* dst[8] = {&c.st->n_inserted, &c.st->n_conflicts, &c.st->n_attempts, &c.st->sum_cavity,
+                                  &c.st->sum_ball, &c.st->sum_walk, &c.st->n_restart, &c.st->n_inserted_async};
+    w.cnt[7] = w.cnt[0];
+    for (int k = 0; k < 8; ++k)
+      if (w.cnt[k]) atomicAdd(dst[k], (unsigned long long)w.cnt[k]);
+  }
+}
+
+// Folds the allocator of the launch into the free list, as a round close does
+// (finish_round_block): the slots freed during the launch (pending) follow the free-list
+// entries it did not consume. Copy on the whole grid, then the state on one thread.
+__global__ void k_async_close_copy(Ctx c) {
+  const DevState* st = c.st;
+  const unsigned long long used = __ldcg(&st->alloc_cursor), fa = __ldcg(&st->free_avail);
+  const unsigned long long consumed = used < fa ? used : fa, nfa = fa - consumed;
+  unsigned long long np = __ldcg(&st->pending);
+  if (nfa + np > st->free_capacity) np = st->free_capacity - nfa;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < np;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    c.freelist[nfa + i] = __ldcg(&c.pending[i]);
+}
+
+__global__ void k_async_close_state(Ctx c) {
+  DevState* st = c.st;
+  const unsigned long long used = st->alloc_cursor, fa = st->free_avail;
+  const unsigned long long consumed = used < fa ? used : fa, nfa = fa - consumed;
+  unsigned long long np = st->pending;
+  if (nfa + np > st->free_capacity) {
+    raise_error(st, kErrFreeList, 0xAAu);
+    np = st->free_capacity - nfa;
+  }
+  st->bump += used - consumed;
+  st->free_avail = nfa + np;
+  st->alloc_cursor = 0;
+  st->pending = 0;
+  st->stamp += 1;
+  st->blocks_done = 0;
+}
+
+int g_async_blocks = 0;  // resident blocks per SM the kernel is built for (0: not chosen yet)
+
+int async_blocks_per_sm() {
+  if (!g_async_blocks) {
+    // 8 resident blocks (32 warps) per SM at 64 registers measured fastest: 255 ms per 1e7 uniform
+    // step against 265 (6 blocks, 80 registers), 276 (5, 96) and 301 (4, 128)
+    int v = 8;
+    if (const char* e = std::getenv("DT_ASYNC_BLOCKS")) v = std::atoi(e);
+    g_async_blocks = (v == 4 || v == 5 || v == 6 || v == 8) ? v : 8;
+  }
+  return g_async_blocks;
+}
+
+}  // namespace
+
+int async_launch(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t* vflag, const InsertLog& lg,
+                 cudaStream_t s) {
+  if (io.W == 0 || io.m == 0) return DT_OK;
+  Ctx cc = c;
+  cc.coherent = 1;
+  cc.max_walk = io.max_walk;
+  const unsigned blocks = (io.W + kAW - 1) / kAW;
+  switch (async_blocks_per_sm()) {
+    case 4: k_async<4><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
+    case 5: k_async<5><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
+    case 6: k_async<6><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
+    default: k_async<8><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
+  }
+  k_async_close_copy<<<152, 256, 0, s>>>(cc);
+  k_async_close_state<<<1, 1, 0, s>>>(cc);
+  g_kernel_launches += 3;
+  return cudaPeekAtLastError() == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
+int async_max_warps() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int mb = async_blocks_per_sm();
+    cudaError_t e = mb == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<4>, kAW * 32, 0)
+                  : mb == 5 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<5>, kAW * 32, 0)
+                  : mb == 6 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<6>, kAW * 32, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<8>, kAW * 32, 0);
+    if (e != cudaSuccess) per = mb;
+    cached = std::max(1, sms * std::max(per, 1) * kAW);
+  }
+  return cached;
+}
+
+}  // namespace dtg

@@ -56,9 +56,10 @@ struct DevState {
   unsigned long long alloc_cursor;   // virtual allocation cursor of this round
   unsigned long long pending;        // slots freed this round (appended after the round)
   unsigned long long free_capacity;  // size of the free-list array
-  unsigned long long q[5];           // queue lengths: 0 next pass, 1 large cavities,
+  unsigned long long q[6];           // queue lengths: 0 next pass, 1 large cavities,
                                      // 2 large-cavity retries, 3 serial path,
-                                     // 4 cavities too large for the shared-memory large rounds
+                                     // 4 cavities too large for the shared-memory large rounds,
+                                     // 5 points the asynchronous engine hands to the rounds
   unsigned int blocks_done;          // blocks of the insert kernel that finished this round
   unsigned int pad1;
   unsigned int error;                // first DevError raised
@@ -68,6 +69,8 @@ struct DevState {
   // statistics
   unsigned long long n_inserted, n_conflicts, n_attempts, n_walk_limit, n_big, n_dups;
   unsigned long long sum_cavity, sum_ball, sum_walk, n_exact, n_sos, max_walk;
+  unsigned long long n_restart;  // asynchronous insertions restarted after a failed re-read
+  unsigned long long n_inserted_async;  // insertions made by the asynchronous engine
 };
 
 __device__ __forceinline__ void raise_error(DevState* st, unsigned int code, unsigned int info) {

@@ -21,6 +21,7 @@ namespace {
 constexpr int kCavWarps = 4;  // candidates per block of the cavity kernel (4 measured faster than 8)
 constexpr int kInsWarps = 8;  // candidates per block of the ball kernel
 constexpr uint32_t kDefaultWalk = 48;          // walk steps per pass (a longer walk resumes next pass)
+constexpr uint32_t kAsyncWalk = 4096;          // walk steps per attempt of the asynchronous engine
 constexpr uint64_t kLongWalkBelow = 8192;      // retry lists shorter than this walk up to
 constexpr uint32_t kLongWalkSteps = 1u << 14;  // this many steps per pass
 constexpr uint32_t kScratchStride = kCMax + kFMax;
@@ -31,6 +32,7 @@ constexpr int kQBig = 1;    // cavity too large for shared memory: large-cavity 
 constexpr int kQBig2 = 2;   // lost a conflict in a large-cavity round: next large-cavity round
 constexpr int kQHuge = 3;   // cavity too large even for the large-cavity workspace: serial path
 constexpr int kQBigG = 4;   // cavity too large for the shared-memory large rounds: global-memory rounds
+constexpr int kQExact = 5;  // the asynchronous engine could not decide a predicate: round-based rounds
 
 // Large-cavity rounds, first tier: one warp per candidate with its workspaces in dynamic shared
 // memory (kMedWarps warps per block), for cavities of up to kMedCN tetrahedra and kMedFN
@@ -240,7 +242,8 @@ __global__ void __launch_bounds__((kInsWarps > kMedWarps ? kInsWarps : kMedWarps
       c.cell_hint[f] = s0;
       c.cell_hint2[g] = s0;
       c.point_hint[p] = s0;
-      c.st->anchor = s0;
+      // the handle's state line also takes the allocator's atomics: refresh the anchor rarely
+      if ((p & 63u) == 0) c.st->anchor = s0;
       atomicAdd(&s_stat[0], 1ull);
       atomicAdd(&s_stat[3], (unsigned long long)nc);
       atomicAdd(&s_stat[4], (unsigned long long)nb);
@@ -781,6 +784,7 @@ struct dt_handle {
   uint64_t n_pts = 0, cap_pts = 0;
   Tet* tets = nullptr;
   unsigned long long* claim = nullptr;
+  uint32_t* lock = nullptr;  // asynchronous engine: owner of each slot (0 = free)
   uint64_t cap_tets = 0;
   uint32_t* freelist = nullptr;
   uint32_t* pending = nullptr;
@@ -794,7 +798,7 @@ struct dt_handle {
   uint32_t Rmax = 0;
   uint32_t *cand_p = nullptr, *cand_t = nullptr, *cand_status = nullptr, *cand_nc = nullptr,
            *cand_nb = nullptr, *scratch = nullptr;
-  uint32_t* queue[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // see kQNext .. kQBigG
+  uint32_t* queue[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // see kQNext .. kQExact
   uint32_t* medscratch = nullptr;  // cavity lists of the shared-memory large rounds
   uint64_t cap_q = 0;
   char* bigmem = nullptr;   // kBigR large-cavity workspaces
@@ -811,6 +815,10 @@ struct dt_handle {
   double gamma = 0.3;    // wave size = gamma * mesh vertices
   double alpha_cta = 0.05; // candidates per round of the one-block engine per mesh vertex (at most 32)
   int walk_threads = 64;   // block size of the thread-per-point walk: small blocks spread a round over every SM
+  bool use_async = true;   // waves and long retry lists run on the asynchronous engine (async.cu)
+  double alpha_async = 0.02; // concurrent insertions (warps) per mesh vertex of the asynchronous engine
+  uint64_t async_min_retry = 2048; // retry lists shorter than this use the round-based engine
+  uint64_t async_warps = 0;        // cap on the asynchronous engine's warps (0: all that fit)
   bool big_smem = true;    // large cavities try the shared-memory workspaces first
   int big_smem_skip = 0;   // passes left that go straight to the global-memory tier
   uint32_t* wlist = nullptr;
@@ -929,6 +937,29 @@ InsertLog make_log(dt_handle* h) {
   return InsertLog{logging ? h->log_nc : nullptr, logging ? h->log_lost : nullptr};
 }
 
+// Device bytes the handle holds (its arrays at their current capacities; the batch and
+// refinement workspaces are counted when they exist).
+uint64_t device_bytes(const dt_handle* h) {
+  uint64_t b = 0;
+  b += h->cap_pts * (sizeof(Pt) + sizeof(PtF) + 1 + 4);             // points, FP32 copy, flag, hint
+  b += h->cap_tets * (sizeof(Tet) + 16 + 4);                         // records, claim pair, owner word
+  b += h->cap_free * 8;                                              // free list and pending
+  if (h->cell_hint_cb > 0) {
+    const int cb = h->cell_hint_cb, cbc = cb > 3 ? cb - 3 : 1;
+    b += (4ull << (3 * cb)) + (4ull << (3 * cbc));
+  }
+  b += h->ows.cap * (8 + 8 + 8 + 4 + 4 + 1 + 1 + 4 + 4) + h->ows.hist_cap * 4;
+  if (h->cand_p) {
+    b += (uint64_t)h->Rmax * (5 * 4 + (uint64_t)kScratchStride * 4);
+    b += h->bigstride * kBigR + (uint64_t)kBigR * (kMedCN + kMedFN) * 4 + h->ctastride * kCtaWarps;
+  }
+  b += h->cap_q * 4 * 5 + h->cap_w * 4;
+  if (h->hugemem) b += carve(nullptr, 4 * h->huge_c, h->huge_c, h->huge_c, 4 * h->huge_c, nullptr);
+  b += h->cap_log * 3 + h->cap_feat * (8 + 2) * 4 + h->cap_risky * 2 + h->cap_cells * 4;
+  b += h->cap_bpts * 32 + h->cap_bws + h->cap_bstates * sizeof(DevState);
+  return b;
+}
+
 int sync_state(dt_handle* h) {
   if (cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return DT_ECUDA;
@@ -959,10 +990,22 @@ int reserve_tets(dt_handle* h, uint64_t total_pts) {
   if (need <= h->cap_tets) return DT_OK;
   unsigned long long bump = h->has_mesh ? h->st_host->bump : 0;
   if (grow(h->tets, bump, need, h->stream) != cudaSuccess) return DT_ENOMEM;
+  // slots not yet handed out read as dead (v.x == v.y == 0): the asynchronous engine may read
+  // a slot through a freshly written pointer before its record arrives, and must never find an
+  // old, self-consistent mesh there
+  cudaMemsetAsync(h->tets + bump, 0, (need - bump) * sizeof(Tet), h->stream);
   if (grow(h->claim, 2 * bump, 2 * need, h->stream) != cudaSuccess) return DT_ENOMEM;
   // claim words of slots not yet handed out start at zero (below every priority)
   cudaMemsetAsync(h->claim + 2 * bump, 0, 2 * (need - bump) * sizeof(unsigned long long), h->stream);
-  uint64_t nf = need / 4 + 4096;
+  // owner words: every slot free (no lock is held between launches)
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->lock);
+  h->lock = nullptr;
+  if (cudaMalloc(&h->lock, need * sizeof(uint32_t)) != cudaSuccess) return DT_ENOMEM;
+  cudaMemsetAsync(h->lock, 0, need * sizeof(uint32_t), h->stream);
+  // free list: the slots a round frees, plus every warp's private slots that the asynchronous
+  // engine hands back when its launch ends
+  uint64_t nf = need / 4 + 4096 + (uint64_t)async_max_warps() * 160;
   uint64_t fold = h->has_mesh ? h->st_host->free_avail : 0;
   if (grow(h->freelist, fold, nf, h->stream) != cudaSuccess) return DT_ENOMEM;
   cudaFree(h->pending);
@@ -1157,7 +1200,45 @@ int run_big(dt_handle* h, const Ctx& c) {
 // One pass: rounds over q[0..m) (or the vertex range qbase + [0, m)) split into R segments of
 // length L (segment s offers q[s*L + j] in round j), then the large cavities of the pass.
 int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next,
-             float alpha_scale = 1.f) {
+             float alpha_scale = 1.f, bool rounds_only = false);
+
+int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next) {
+  uint64_t mesh = h->st_host->n_inserted;
+  uint64_t W = (uint64_t)std::max(1.0, h->alpha_async * (double)mesh);
+  W = std::min<uint64_t>(W, h->async_warps ? h->async_warps : (uint64_t)async_max_warps());
+  W = std::min<uint64_t>(W, m);
+  const uint64_t L = (m + W - 1) / W;
+  W = (m + L - 1) / L;
+  int rc = reset_next ? set_queue_lengths(h, {kQNext, kQBig, kQHuge}) : set_queue_lengths(h, {kQBig, kQHuge});
+  if (rc != DT_OK) return rc;
+  if ((rc = set_queue_lengths(h, {kQExact})) != DT_OK) return rc;
+  AsyncIO io{q, qbase, m, L, (uint32_t)W, h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kAsyncWalk,
+             h->queue[kQNext], kQNext, h->queue[kQBig], kQBig, h->queue[kQExact], kQExact};
+  const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0;
+  if (prof) cudaEventRecord(h->ev[3], h->stream);
+  if ((rc = async_launch(c, io, h->lock, h->vflag, make_log(h), h->stream)) != DT_OK) return rc;
+  if (prof) cudaEventRecord(h->ev[4], h->stream);
+  h->stats.n_async++;
+  h->stats.n_passes++;
+  if ((rc = sync_state(h)) != DT_OK) return rc;
+  if (prof) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]);
+    h->stats.ms_async += ms;
+  }
+  if ((rc = run_big(h, c)) != DT_OK) return rc;
+  // points whose predicates the asynchronous engine's FP32 stage could not decide: one
+  // round-based pass with the full predicate cascade (its losers join the next pass's list)
+  const uint64_t ne = h->st_host->q[kQExact];
+  if (ne == 0) return DT_OK;
+  h->stats.n_exact_handoff += ne;
+  return run_pass(h, c, h->queue[kQExact], 0, ne, false, 1.f, true);
+}
+
+int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next,
+             float alpha_scale, bool rounds_only) {
+  if (h->use_async && !rounds_only && (!reset_next || m >= h->async_min_retry))
+    return run_pass_async(h, c, q, qbase, m, reset_next);
   uint64_t& kind_rounds = reset_next ? h->stats.n_rounds_retry : h->stats.n_rounds_wave;
   uint64_t mesh = h->st_host->n_inserted;
   uint32_t R = choose_segments(h, mesh, m, alpha_scale);
@@ -1399,6 +1480,8 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
     }
     cudaMemsetAsync(h->cell_hint, 0xFF, (size_t)4 << (3 * cb), s);
     cudaMemsetAsync(h->cell_hint2, 0xFF, (size_t)4 << (3 * cbc), s);
+    // a new mesh: every slot reads as dead until it is handed out (see reserve_tets)
+    cudaMemsetAsync(h->tets, 0, h->cap_tets * sizeof(Tet), s);
     DevState z{};
     z.stamp = h->next_stamp;
     z.capacity = h->cap_tets;
@@ -1899,6 +1982,9 @@ void fill_stats(dt_handle* h, dt_stats* o) {
   o->n_walk_limit = d.n_walk_limit;
   o->free_slots = d.free_avail;
   o->max_walk = d.max_walk;
+  o->n_restarts = d.n_restart;
+  o->n_inserted_async = d.n_inserted_async;
+  o->device_bytes = device_bytes(h);
 }
 
 }  // namespace
@@ -1922,6 +2008,10 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (const char* g = std::getenv("DT_GAMMA")) h->gamma = std::atof(g);
   if (const char* a = std::getenv("DT_ALPHA_CTA")) h->alpha_cta = std::atof(a);
   if (const char* b = std::getenv("DT_BIG_SMEM")) h->big_smem = std::atoi(b) != 0;
+  if (const char* a = std::getenv("DT_ASYNC")) h->use_async = std::atoi(a) != 0;
+  if (const char* a = std::getenv("DT_ALPHA_ASYNC")) h->alpha_async = std::atof(a);
+  if (const char* a = std::getenv("DT_ASYNC_MIN_RETRY")) h->async_min_retry = std::strtoull(a, nullptr, 10);
+  if (const char* a = std::getenv("DT_ASYNC_WARPS")) h->async_warps = std::strtoull(a, nullptr, 10);
   if (const char* w = std::getenv("DT_WALK_THREADS")) {
     int v = std::atoi(w);
     if (v == 32 || v == 64 || v == 128 || v == 256) h->walk_threads = v;
@@ -2228,6 +2318,7 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->point_hint);
   cudaFree(h->tets);
   cudaFree(h->claim);
+  cudaFree(h->lock);
   cudaFree(h->freelist);
   cudaFree(h->pending);
   cudaFree(h->cell_hint);

@@ -72,6 +72,12 @@ int main(int argc, char** argv) {
               (unsigned long long)st.n_rounds, (unsigned long long)st.n_passes,
               (unsigned long long)st.n_attempts, (unsigned long long)st.n_conflicts,
               (unsigned long long)st.n_launches);
+  std::printf("async launches %llu restarts %llu handoffs %llu walk steps %llu big %llu exact %llu ms_sort %.2f "
+              "ms_first %.2f device bytes %llu\n",
+              (unsigned long long)st.n_async, (unsigned long long)st.n_restarts,
+              (unsigned long long)st.n_exact_handoff, (unsigned long long)st.sum_walk,
+              (unsigned long long)st.n_big, (unsigned long long)st.n_exact, st.ms_sort, st.ms_first_round,
+              (unsigned long long)st.device_bytes);
   dt_destroy(h);
   cudaFree(d);
   return rc ? 1 : 0;

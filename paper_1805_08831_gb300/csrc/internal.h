@@ -124,8 +124,33 @@ uint64_t brio_round_end(int r);
 void transformed_keys(const Pt* pts, const uint32_t* ids, uint64_t m, const double* bbox,
                       uint64_t seed, uint64_t* keys_out, uint32_t* vals_out, cudaStream_t s);
 
-// ---------------------------------------------------------------- batch.cu (dt_batch)
+// ---------------------------------------------------------------- async.cu (one launch per pass)
 struct Ctx;
+struct InsertLog;
+// Points q[0, m) (or the vertex range qbase + [0, m) when q is null) in W contiguous segments
+// of L points, segment w inserted by warp w in order. Points that lose or walk past max_walk
+// steps go to lose_out (queue lose_q), cavities too large for a warp's workspace to big_out.
+struct AsyncIO {
+  const uint32_t* q;
+  uint32_t qbase;
+  uint64_t m, L;
+  uint32_t W;
+  uint32_t max_walk;
+  uint32_t* lose_out;
+  int lose_q;
+  uint32_t* big_out;
+  int big_q;
+  uint32_t* exact_out;  // predicates the FP32 stage cannot decide: the round-based engine's
+  int exact_q;
+};
+// Enqueues the asynchronous insertion of one pass and the close of its allocator. lock: one
+// word per tetrahedron slot, all zero before and after.
+int async_launch(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t* vflag, const InsertLog& lg,
+                 cudaStream_t s);
+// Warps of the asynchronous kernel that can be resident on the current device at once.
+int async_max_warps();
+
+// ---------------------------------------------------------------- batch.cu (dt_batch)
 size_t batch_ws_stride();       // bytes of one warp's workspace
 uint32_t batch_hint_fine();     // fine hint cells per cloud
 uint32_t batch_hint_coarse();   // coarse hint cells per cloud

@@ -65,3 +65,15 @@ def test_cpu_paper_scheme_leg_reports_an_exact_rate():
     assert leg["bit_exact_vs_oracle"] is True and leg["cores"] == (os.cpu_count() or 1)
     assert leg["value"] > 0 and leg["unit"] == "Mtets/s" and leg["passes"] >= 3
     assert np.isfinite(leg["value"])
+
+
+def test_path_bytes_are_the_tables_terms():
+    """The bench's algorithmic bytes per inserted point: the hot-path table's formula with the
+    paper's mean cavity (|C| = 20) and ball (|B| = 26) and two walk steps, worked by hand:
+    walk 2 * 104 = 208; cavity 46 * 32 + (15 + 26) * 24 + 46 * 8 = 1472 + 984 + 368 = 2824;
+    ball 26 * 32 + 26 * 4 + 20 * 4 + 46 * 4 = 832 + 104 + 80 + 184 = 1200."""
+    import bench
+    st = {"n_unique": 1000, "sum_cavity": 20000, "sum_ball": 26000, "sum_walk": 4000, "n_attempts": 2000}
+    terms, cfb = bench.path_bytes(st)
+    assert cfb["V"] == 15.0 and cfb["w"] == 2.0
+    assert terms == {"walk": 208.0, "cavity": 2824.0, "ball": 1200.0}

@@ -68,6 +68,7 @@ struct AsyncWS {
   unsigned long long fa, bump;  // allocator snapshot of the launch
   unsigned int cnt[8];          // inserted, lost, attempts, sum |C|, sum |B|, walk steps, restarts
   uint32_t hint;                // the warp's last ball
+  int bn;                       // tetrahedra of the warp's last ball (0: none); slots in slot[]
   int np;                       // slots in the pool
   int nc, na, nb;               // cavity, outside and boundary-facet counts of the last search
   union {
@@ -107,15 +108,22 @@ __device__ __forceinline__ bool rec_ok(const Tet& T, uint32_t ntets, uint32_t np
 // perturbation): keeping the exact stages out of this kernel keeps its registers free of the
 // save and restore traffic their calls would cost. A return of 0 means "undecided".
 
-// orient3d of (v0, v1, v2, v3) with vertex i replaced by p.
+__device__ __forceinline__ PtF pick(bool c, const PtF& x, const PtF& y) {
+  PtF r;
+  r.hx = c ? x.hx : y.hx; r.hy = c ? x.hy : y.hy; r.hz = c ? x.hz : y.hz; r.hw = 0.f;
+  r.lx = c ? x.lx : y.lx; r.ly = c ? x.ly : y.ly; r.lz = c ? x.lz : y.lz; r.lw = 0.f;
+  return r;
+}
+
+// orient3d of (v0, v1, v2, v3) with vertex i replaced by p. Moving p to the last place is an
+// odd permutation for i = 0, 2 and an even one for i = 1, 3, so one FP32 evaluation on the other
+// three vertices in their order serves every i (one copy of the code: the kernel's instruction
+// footprint decides how often its warps wait for instructions).
 __device__ __forceinline__ int orient_with_p(const Ctx& c, int i, const PtF& FP, const PtF& F0, const PtF& F1,
                                              const PtF& F2, const PtF& F3) {
-  switch (i) {
-    case 0: return orient3d_f(FP, F1, F2, F3, c.eta);
-    case 1: return orient3d_f(F0, FP, F2, F3, c.eta);
-    case 2: return orient3d_f(F0, F1, FP, F3, c.eta);
-    default: return orient3d_f(F0, F1, F2, FP, c.eta);
-  }
+  const PtF A = pick(i == 0, F1, F0), B = pick(i <= 1, F2, F1), C = pick(i <= 2, F3, F2);
+  const int o = orient3d_f(A, B, C, FP, c.eta);
+  return (i & 1) ? o : -o;
 }
 
 // Insphere of a finite tetrahedron v and p: -1 inside, 1 outside, 0 undecided.
@@ -156,6 +164,7 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
               F3 = load_ptf(c.ptf, T.v.w);
     int exit = -1;
     const int s0 = (salt + steps) & 3;
+#pragma unroll 1
     for (int k = 0; k < 4; ++k) {
       const int i = (s0 + k) & 3;
       if ((get4(T.n, i) >> 2) == prev) continue;
@@ -209,13 +218,10 @@ __device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const 
     const int s = inside_async(c, U.v, FP);
     return s < 0 ? 1 : (s > 0 ? 0 : -2);
   }
-  int o;
-  switch (g) {  // orientation of the hull facet's three vertices and p in the ghost's place
-    case 0: o = orient3d_f(FP, load_ptf(c.ptf, U.v.y), load_ptf(c.ptf, U.v.z), load_ptf(c.ptf, U.v.w), c.eta); break;
-    case 1: o = orient3d_f(load_ptf(c.ptf, U.v.x), FP, load_ptf(c.ptf, U.v.z), load_ptf(c.ptf, U.v.w), c.eta); break;
-    case 2: o = orient3d_f(load_ptf(c.ptf, U.v.x), load_ptf(c.ptf, U.v.y), FP, load_ptf(c.ptf, U.v.w), c.eta); break;
-    default: o = orient3d_f(load_ptf(c.ptf, U.v.x), load_ptf(c.ptf, U.v.y), load_ptf(c.ptf, U.v.z), FP, c.eta); break;
-  }
+  // orientation of the hull facet's three vertices and p in the ghost's place
+  const uint32_t a = g == 0 ? U.v.y : U.v.x, b = g <= 1 ? U.v.z : U.v.y, d = g <= 2 ? U.v.w : U.v.z;
+  int o = orient3d_f(load_ptf(c.ptf, a), load_ptf(c.ptf, b), load_ptf(c.ptf, d), FP, c.eta);
+  o = (g & 1) ? o : -o;
   if (o != 0) return o > 0 ? 1 : 0;
   // p on the facet's plane as far as the FP32 stage can tell: the exact rule needs the
   // round-based engine (the plane test and the neighbour's perturbed sphere)
@@ -226,6 +232,7 @@ __device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const 
 
 __device__ __forceinline__ int hfind(const AsyncWS& w, uint32_t key) {
   uint32_t h = (hash32(key) >> 8) & (kAHash - 1);
+#pragma unroll 1
   for (int probe = 0; probe < kAHash; ++probe) {
     uint32_t k = vld(&w.hkey[h]);
     if (k == key) return vld(&w.hval[h]);
@@ -237,6 +244,7 @@ __device__ __forceinline__ int hfind(const AsyncWS& w, uint32_t key) {
 
 __device__ __forceinline__ bool hinsert(AsyncWS& w, uint32_t key, uint8_t val) {
   uint32_t h = (hash32(key) >> 8) & (kAHash - 1);
+#pragma unroll 1
   for (int probe = 0; probe < kAHash; ++probe) {
     uint32_t old = atomicCAS(&w.hkey[h], kNone, key);
     if (old == kNone || old == key) {
@@ -249,57 +257,39 @@ __device__ __forceinline__ bool hinsert(AsyncWS& w, uint32_t key, uint8_t val) {
 }
 
 // Step 2: the cavity of p from t0 on unlocked reads. Returns kAInserted (lists filled),
-// kARestart (an inconsistent read) or kABig (the workspace is too small).
+// kARestart (an inconsistent read), kABig (the workspace is too small) or kAExact. The first
+// pass of the loop tests t0 itself (one lane), so the conflict test's code exists once.
 __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t0, uint32_t p, const PtF& FP) {
   const int lane = threadIdx.x & 31;
   for (int i = lane; i < kAHash; i += 32) w.hkey[i] = kNone;
   __syncwarp();
   int flag = 0;  // 1 restart, 2 big, 4 a predicate the FP32 stage cannot decide
-  if (lane == 0) {
-    const Tet T = ld_tet(c.tets, t0);
-    uint32_t r = kNone;
-    uint4 rv{};
-    const int in = (tet_dead(T.v) || !rec_ok(T, c.ntets, c.npts)) ? -1 : conflict_async(c, T, FP, &r, &rv);
-    int na = 0;
-    if (in == -2) {
-      flag = 4;
-    } else if (in != 1) {
-      flag = 1;
-    } else {
-      w.cl[0] = t0;
-      w.cr[0] = T;
-      hinsert(w, t0, 1);
-      if (r != kNone) {
-        w.al[0] = r | kVerifyOnly;
-        w.av[0] = rv;
-        na = 1;
-      }
-    }
-    w.nc = 1;
-    w.na = na;
-    w.nb = 0;
-  }
-  flag = __shfl_sync(kFull, flag, 0);
-  __syncwarp();
-  if (flag & 4) return kAExact;
-  if (flag) return kARestart;
-  int nc = 1, na = w.na, nb = 0, head = 0;
-  while (head < nc && flag == 0) {
-    const int batch = min(8, nc - head);
+  int nc = 0, na = 0, nb = 0, head = 0;
+  bool seed = true;
+  while (flag == 0 && (seed || head < nc)) {
     const int k = lane >> 2, f = lane & 3;
-    bool active = k < batch;
-    const int ci = head + k;
+    bool active;
+    int ci;
     uint32_t u = kNone;
-    if (active) {
-      u = get4(w.cr[ci].n, f) >> 2;
-      if (u >= c.ntets) {
-        flag = 1;
-        active = false;
+    if (seed) {
+      active = lane == 0;
+      ci = -1;
+      u = t0;
+    } else {
+      const int batch = min(8, nc - head);
+      active = k < batch;
+      ci = head + k;
+      if (active) {
+        u = get4(w.cr[ci].n, f) >> 2;
+        if (u >= c.ntets) {
+          flag = 1;
+          active = false;
+        }
       }
+      flag = __reduce_or_sync(kFull, flag);
+      if (flag) break;
+      head += batch;
     }
-    flag = __reduce_or_sync(kFull, flag);
-    if (flag) break;
-    head += batch;
     const int known = active ? hfind(w, u) : 0;
     const bool need = active && known == 0;
     const unsigned peers = __match_any_sync(kFull, need ? u : 0xFFFFFFFFu);
@@ -318,11 +308,14 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
         myflag |= 1;
       } else {
         res = in ? 1 : 2;
-        if (!hinsert(w, u, (uint8_t)res)) myflag |= 2;
+        if (seed && res != 1) myflag |= 1;  // the walk's tetrahedron was read mid-rewrite
+        else if (!hinsert(w, u, (uint8_t)res)) myflag |= 2;
       }
     }
     const int lres = __shfl_sync(kFull, res, leader);
     res = need ? lres : known;
+    flag = __reduce_or_sync(kFull, myflag);
+    if (flag) break;
     const bool addC = is_leader && res == 1;
     const unsigned mC = __ballot_sync(kFull, addC);
     if (addC) {
@@ -353,7 +346,7 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
       }
     }
     na += __popc(mR);
-    const bool addB = active && res == 2;
+    const bool addB = active && ci >= 0 && res == 2;
     const unsigned mB = __ballot_sync(kFull, addB);
     if (addB) {
       const int pos = nb + __popc(mB & lanemask_lt());
@@ -363,8 +356,8 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
       }
     }
     nb += __popc(mB);
-    flag = __reduce_or_sync(kFull, myflag);
     if (nc > kACMax || na > kAAMax || nb > kAFMax) flag |= 2;
+    seed = false;
     __syncwarp();
   }
   if (lane == 0) {
@@ -451,10 +444,22 @@ __device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lo
   const int lane = threadIdx.x & 31;
   const PtF FP = load_ptf(c.ptf, p);
   for (int attempt = 0; attempt <= kARetry; ++attempt) {
-    // 1. walk (one lane)
-    int ws = 0;
+    // 1. a start in conflict with p. Consecutive points of a segment are close, so p is often
+    //    inside the circumsphere of a tetrahedron of the previous ball (it will be joined to the
+    //    previous point): one insphere test per lane finds it without a walk. Otherwise walk.
+    int ws = kAInserted;
     uint32_t t0 = kNone;
-    if (lane == 0) {
+    if (attempt == 0 && w.bn > 0) {
+      bool in = false;
+      if (lane < w.bn) {
+        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(c.tets + w.slot[lane]));
+        in = !tet_dead(v) && ghost_pos(v) < 0 && v.x < c.npts && v.y < c.npts && v.z < c.npts && v.w < c.npts &&
+             inside_async(c, v, FP) < 0;
+      }
+      const unsigned m = __ballot_sync(kFull, in);
+      if (m) t0 = w.slot[__ffs(m) - 1];
+    }
+    if (t0 == kNone && lane == 0) {
       uint32_t start = attempt == 0 ? w.hint : c.point_hint[p];
       if (start == kNone) start = c.point_hint[p];
       if (start == kNone) {
@@ -470,6 +475,7 @@ __device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lo
     }
     ws = __shfl_sync(kFull, ws, 0);
     t0 = __shfl_sync(kFull, t0, 0);
+    if (lane == 0) w.bn = 0;  // used once
     if (ws == kADup || ws == kAWalkLimit || ws == kAExact) return ws;
     if (ws == kARestart) {
       if (lane == 0) w.cnt[6] += 1;
@@ -593,6 +599,7 @@ __device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lo
       if ((w.cnt[0] & 63u) == 0) c.st->anchor = s0;
       log_outcome(lg, p, kCandInserted, nc);
       w.hint = s0;
+      w.bn = nb < 32 ? nb : 32;
       w.cnt[0] += 1;
       w.cnt[3] += nc;
       w.cnt[4] += nb;
@@ -627,6 +634,7 @@ __global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO i
     w.fa = __ldcg(&c.st->free_avail);
     w.bump = __ldcg(&c.st->bump);
     w.np = 0;
+    w.bn = 0;
     for (int k = 0; k < 8; ++k) w.cnt[k] = 0;
     w.hint = b0 < e0 ? c.point_hint[io.q ? io.q[b0] : io.qbase + (uint32_t)b0] : kNone;
   }

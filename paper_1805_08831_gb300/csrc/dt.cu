@@ -33,6 +33,8 @@ constexpr int kQBig2 = 2;   // lost a conflict in a large-cavity round: next lar
 constexpr int kQHuge = 3;   // cavity too large even for the large-cavity workspace: serial path
 constexpr int kQBigG = 4;   // cavity too large for the shared-memory large rounds: global-memory rounds
 constexpr int kQExact = 5;  // the asynchronous engine could not decide a predicate: round-based rounds
+constexpr int kNumQueues = 6;
+static_assert(sizeof(DevState::q) / sizeof(DevState::q[0]) == kNumQueues, "one length per queue");
 
 // Large-cavity rounds, first tier: one warp per candidate with its workspaces in dynamic shared
 // memory (kMedWarps warps per block), for cavities of up to kMedCN tetrahedra and kMedFN
@@ -798,7 +800,7 @@ struct dt_handle {
   uint32_t Rmax = 0;
   uint32_t *cand_p = nullptr, *cand_t = nullptr, *cand_status = nullptr, *cand_nc = nullptr,
            *cand_nb = nullptr, *scratch = nullptr;
-  uint32_t* queue[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // see kQNext .. kQExact
+  uint32_t* queue[kNumQueues] = {};  // kQNext .. kQExact
   uint32_t* medscratch = nullptr;  // cavity lists of the shared-memory large rounds
   uint64_t cap_q = 0;
   char* bigmem = nullptr;   // kBigR large-cavity workspaces
@@ -1202,6 +1204,7 @@ int run_big(dt_handle* h, const Ctx& c) {
 int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next,
              float alpha_scale = 1.f, bool rounds_only = false);
 
+
 int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next) {
   uint64_t mesh = h->st_host->n_inserted;
   uint64_t W = (uint64_t)std::max(1.0, h->alpha_async * (double)mesh);
@@ -1226,6 +1229,8 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
     cudaEventElapsedTime(&ms, h->ev[3], h->ev[4]);
     h->stats.ms_async += ms;
   }
+  // large cavities now (deferring them to the end of the BRIO round was measured slower: they
+  // then meet each other, 592 instead of 395 rounds per 1e7 uniform step)
   if ((rc = run_big(h, c)) != DT_OK) return rc;
   // points whose predicates the asynchronous engine's FP32 stage could not decide: one
   // round-based pass with the full predicate cascade (its losers join the next pass's list)
@@ -1390,7 +1395,9 @@ int run_brio_round(dt_handle* h, uint32_t vbegin, uint32_t vend, int round, uint
     // a short retry list is cheap per round: let its walks run long instead of over many passes
     Ctx cr = c;
     if (!h->cfg.max_walk_steps && nq < kLongWalkBelow) cr.max_walk = kLongWalkSteps;
-    if ((rc = run_pass(h, cr, a2 ? h->ows.v1 : h->ows.v0, 0, nq, true)) != DT_OK) return rc;
+    // after a pass that made no progress the round-based engine takes over: its highest-priority
+    // located point always wins, where the asynchronous engine's retries might keep colliding
+    if ((rc = run_pass(h, cr, a2 ? h->ows.v1 : h->ows.v0, 0, nq, true, 1.f, stalled > 0)) != DT_OK) return rc;
     nq = h->st_host->q[kQNext];
     // every pass shrinks the retry list (its highest-priority located point is inserted, or
     // moves to the large-cavity queue) or advances walks that hit their step limit; three

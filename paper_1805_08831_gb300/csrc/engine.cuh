@@ -453,6 +453,7 @@ constexpr uint32_t kNoVertex = kDeadMark;
 
 __device__ __forceinline__ int vslot(uint32_t* vkey, uint32_t x) {
   uint32_t h = hash32(x) >> 27;
+#pragma unroll 1
   for (int probe = 0; probe < 32; ++probe) {
     uint32_t old = atomicCAS(&vkey[h], kNoVertex, x);
     if (old == kNoVertex || old == x) return (int)h;

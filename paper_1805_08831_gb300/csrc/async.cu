@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 #include "engine.cuh"
@@ -37,12 +38,7 @@
 namespace dtg {
 namespace {
 
-constexpr int kAW = 4;            // warps per block
-constexpr int kAHash = 256;       // visited-set slots per warp
-constexpr int kACMax = 64;        // cavity tetrahedra
-constexpr int kAAMax = 64;        // outside tetrahedra (+ verify-only records)
-constexpr int kAFMax = 60;        // boundary facets (<= 32 boundary vertices: the 32 x 32 edge table)
-constexpr int kAPool = 96;        // private free slots
+constexpr int kAW = 4;            // warps per block of the shared-memory kernel
 constexpr int kADefer = 16;       // aborted points waiting for a retry
 constexpr int kARetry = 3;        // immediate restarts after a failed re-read
 constexpr uint32_t kAChunk = 32;  // slots taken from the allocator at a time
@@ -50,35 +46,68 @@ constexpr uint32_t kVerifyOnly = 0x80000000u;  // outside-list entry read but no
 
 enum AStatus : int { kAInserted = 0, kALost = 1, kARestart = 2, kABig = 3, kAWalkLimit = 4, kADup = 5, kAExact = 6 };
 
-// Shared-memory workspace of one warp. The visited set is needed only while the cavity is
-// searched, the edge table only while the ball is built: they share their bytes.
-struct AsyncWS {
-  uint32_t cl[kACMax];       // cavity slots
-  Tet cr[kACMax];            // their records as read
-  uint32_t al[kAAMax];       // outside slots (kVerifyOnly: read for a ghost test, not locked)
-  uint4 av[kAAMax];          // their vertex ids as read
-  uint32_t slot[kAFMax];     // slots of the new tetrahedra
-  uint32_t ex[kAFMax];       // slots beyond the cavity's, taken from the pool
+// Ball adjacency (Section 2.5): the n x n edge table for balls of at most 32 boundary vertices
+// (the shared-memory workspaces), an edge hash for larger ones (the global-memory workspaces).
+template <bool kTable, int kHashN, int kFMaxN>
+struct AWSTail;
+template <int kHashN, int kFMaxN>
+struct AWSTail<true, kHashN, kFMaxN> {
+  // the visited set is needed only while the cavity is searched, the edge table only while the
+  // ball is built: they share their bytes
+  union {
+    struct {
+      uint32_t hkey[kHashN];
+      uint8_t hval[kHashN];
+    };
+    uint16_t tab[32 * 32];
+  };
+};
+template <int kHashN, int kFMaxN>
+struct AWSTail<false, kHashN, kFMaxN> {
+  static constexpr uint32_t kEdgeN = 4096;
+  uint32_t hkey[kHashN];
+  uint8_t hval[kHashN];
+  unsigned long long ekey[kEdgeN];
+  uint32_t eval[kEdgeN];
+  uint32_t hslot[3 * kFMaxN];
+  uint32_t hold[3 * kFMaxN];
+};
+
+// Working storage of one warp: the cavity's tetrahedra with their records as read, the outside
+// tetrahedra with their vertices as read, the boundary facets, the ball's slots, a private pool
+// of free slots, deferred points, and the warp's state (uniform across its lanes, written by
+// lane 0). Held: the type of a lane's lock mask (one bit per lock-list entry of the lane).
+template <int kHashN, int kCMaxN, int kAMaxN, int kFMaxN, bool kTableB, class HeldT>
+struct AWS : AWSTail<kTableB, kHashN, kFMaxN> {
+  static constexpr int kHash = kHashN, kCMax = kCMaxN, kAMax = kAMaxN, kFMax = kFMaxN;
+  static constexpr int kPool = kFMaxN + 36;  // a refill of 32 slots always fits below kFMax
+  static constexpr bool kTable = kTableB;
+  using Held = HeldT;
+  using CI = typename std::conditional<(kCMaxN > 255), uint16_t, uint8_t>::type;
+  static_assert(kCMaxN + kAMaxN + kFMaxN <= 32 * 8 * (int)sizeof(HeldT), "lock mask holds every entry");
+  uint32_t cl[kCMaxN];       // cavity slots
+  Tet cr[kCMaxN];            // their records as read
+  uint32_t al[kAMaxN];       // outside slots (kVerifyOnly: read for a ghost test, not locked)
+  uint4 av[kAMaxN];          // their vertex ids as read
+  uint32_t slot[kFMaxN];     // slots of the new tetrahedra
+  uint32_t ex[kFMaxN];       // slots beyond the cavity's, taken from the pool
   uint32_t vkey[32];
-  uint32_t pool[kAPool];
+  uint32_t pool[kPool];
   uint32_t defer[kADefer];
-  uint8_t bl_ci[kAFMax];     // boundary facet: cavity index
-  uint8_t bl_f[kAFMax];      // boundary facet: facet
-  // the warp's state, uniform across its lanes (written by lane 0)
+  CI bl_ci[kFMaxN];          // boundary facet: cavity index
+  uint8_t bl_f[kFMaxN];      // boundary facet: facet
   unsigned long long fa, bump;  // allocator snapshot of the launch
   unsigned int cnt[8];          // inserted, lost, attempts, sum |C|, sum |B|, walk steps, restarts
   uint32_t hint;                // the warp's last ball
   int bn;                       // tetrahedra of the warp's last ball (0: none); slots in slot[]
   int np;                       // slots in the pool
   int nc, na, nb;               // cavity, outside and boundary-facet counts of the last search
-  union {
-    struct {
-      uint32_t hkey[kAHash];
-      uint8_t hval[kAHash];
-    };
-    uint16_t tab[32 * 32];
-  };
 };
+
+// Shared-memory workspace of the main kernel (cavities of up to 64 tetrahedra and 60 boundary
+// facets) and the global-memory one of the large-cavity kernel.
+using SmallWS = AWS<256, 64, 64, 60, true, unsigned>;
+using LargeWS = AWS<4096, 640, 704, 704, false, unsigned long long>;
 
 __device__ __forceinline__ Tet ld_tet(const Tet* T, uint32_t t) { return load_tet_cg(T, t); }
 
@@ -230,28 +259,30 @@ __device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const 
   return -2;
 }
 
-__device__ __forceinline__ int hfind(const AsyncWS& w, uint32_t key) {
-  uint32_t h = (hash32(key) >> 8) & (kAHash - 1);
+template <class W>
+__device__ __forceinline__ int hfind(const W& w, uint32_t key) {
+  uint32_t h = (hash32(key) >> 8) & (W::kHash - 1);
 #pragma unroll 1
-  for (int probe = 0; probe < kAHash; ++probe) {
+  for (int probe = 0; probe < W::kHash; ++probe) {
     uint32_t k = vld(&w.hkey[h]);
     if (k == key) return vld(&w.hval[h]);
     if (k == kNone) return 0;
-    h = (h + 1) & (kAHash - 1);
+    h = (h + 1) & (W::kHash - 1);
   }
   return 0;
 }
 
-__device__ __forceinline__ bool hinsert(AsyncWS& w, uint32_t key, uint8_t val) {
-  uint32_t h = (hash32(key) >> 8) & (kAHash - 1);
+template <class W>
+__device__ __forceinline__ bool hinsert(W& w, uint32_t key, uint8_t val) {
+  uint32_t h = (hash32(key) >> 8) & (W::kHash - 1);
 #pragma unroll 1
-  for (int probe = 0; probe < kAHash; ++probe) {
+  for (int probe = 0; probe < W::kHash; ++probe) {
     uint32_t old = atomicCAS(&w.hkey[h], kNone, key);
     if (old == kNone || old == key) {
       w.hval[h] = val;
       return true;
     }
-    h = (h + 1) & (kAHash - 1);
+    h = (h + 1) & (W::kHash - 1);
   }
   return false;
 }
@@ -259,9 +290,10 @@ __device__ __forceinline__ bool hinsert(AsyncWS& w, uint32_t key, uint8_t val) {
 // Step 2: the cavity of p from t0 on unlocked reads. Returns kAInserted (lists filled),
 // kARestart (an inconsistent read), kABig (the workspace is too small) or kAExact. The first
 // pass of the loop tests t0 itself (one lane), so the conflict test's code exists once.
-__device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t0, uint32_t p, const PtF& FP) {
+template <class W>
+__device__ __forceinline__ int cavity_async(const Ctx& c, W& w, uint32_t t0, uint32_t p, const PtF& FP) {
   const int lane = threadIdx.x & 31;
-  for (int i = lane; i < kAHash; i += 32) w.hkey[i] = kNone;
+  for (int i = lane; i < W::kHash; i += 32) w.hkey[i] = kNone;
   __syncwarp();
   int flag = 0;  // 1 restart, 2 big, 4 a predicate the FP32 stage cannot decide
   int nc = 0, na = 0, nb = 0, head = 0;
@@ -320,7 +352,7 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
     const unsigned mC = __ballot_sync(kFull, addC);
     if (addC) {
       const int pos = nc + __popc(mC & lanemask_lt());
-      if (pos < kACMax) {
+      if (pos < W::kCMax) {
         w.cl[pos] = u;
         w.cr[pos] = U;
       }
@@ -332,7 +364,7 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
     const unsigned mA = __ballot_sync(kFull, addA), mR = __ballot_sync(kFull, addR);
     if (addA) {
       const int pos = na + __popc(mA & lanemask_lt());
-      if (pos < kAAMax) {
+      if (pos < W::kAMax) {
         w.al[pos] = u;
         w.av[pos] = U.v;
       }
@@ -340,7 +372,7 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
     na += __popc(mA);
     if (addR) {
       const int pos = na + __popc(mR & lanemask_lt());
-      if (pos < kAAMax) {
+      if (pos < W::kAMax) {
         w.al[pos] = r | kVerifyOnly;
         w.av[pos] = rv;
       }
@@ -350,13 +382,13 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
     const unsigned mB = __ballot_sync(kFull, addB);
     if (addB) {
       const int pos = nb + __popc(mB & lanemask_lt());
-      if (pos < kAFMax) {
-        w.bl_ci[pos] = (uint8_t)ci;
+      if (pos < W::kFMax) {
+        w.bl_ci[pos] = (typename W::CI)ci;
         w.bl_f[pos] = (uint8_t)f;
       }
     }
     nb += __popc(mB);
-    if (nc > kACMax || na > kAAMax || nb > kAFMax) flag |= 2;
+    if (nc > W::kCMax || na > W::kAMax || nb > W::kFMax) flag |= 2;
     seed = false;
     __syncwarp();
   }
@@ -374,7 +406,8 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, AsyncWS& w, uint32_t t
 
 // Slot of lock-list entry i: cavity slots, then the outside slots that are locked, then the
 // ball's extra slots. Verify-only outside entries give kNone (not locked).
-__device__ __forceinline__ uint32_t lock_entry(const AsyncWS& w, int i, int nc, int na, int nx) {
+template <class W>
+__device__ __forceinline__ uint32_t lock_entry(const W& w, int i, int nc, int na, int nx) {
   if (i < nc) return w.cl[i];
   i -= nc;
   if (i < na) {
@@ -386,7 +419,9 @@ __device__ __forceinline__ uint32_t lock_entry(const AsyncWS& w, int i, int nc, 
 }
 
 // Releases the locks of the entries this lane took (bit k of `held` = entry lane + 32 k).
-__device__ __forceinline__ void release_held(const AsyncWS& w, uint32_t* lock, unsigned held, int nc, int na, int nx) {
+template <class W>
+__device__ __forceinline__ void release_held(const W& w, uint32_t* lock, typename W::Held held, int nc, int na,
+                                             int nx) {
   const int lane = threadIdx.x & 31;
   for (int k = 0; held; ++k, held >>= 1)
     if (held & 1u) __stcg(&lock[lock_entry(w, lane + 32 * k, nc, na, nx)], 0u);
@@ -394,7 +429,8 @@ __device__ __forceinline__ void release_held(const AsyncWS& w, uint32_t* lock, u
 
 // Takes n slots from the warp's pool into w.ex, refilling it from the allocator (free list,
 // then the bump pointer, as in the round-based engine). False when the store is full.
-__device__ __forceinline__ bool pool_take(const Ctx& c, AsyncWS& w, int n) {
+template <class W>
+__device__ __forceinline__ bool pool_take(const Ctx& c, W& w, int n) {
   const int lane = threadIdx.x & 31;
   int np = w.np;
   while (np < n) {
@@ -407,7 +443,7 @@ __device__ __forceinline__ bool pool_take(const Ctx& c, AsyncWS& w, int n) {
       if (lane == 0) raise_error(c.st, kErrCapacity, 0xA5u);
       return false;
     }
-    w.pool[np + lane] = s;  // np < n <= kAFMax, so np + 32 <= kAPool
+    w.pool[np + lane] = s;  // np < n <= kFMax, so np + 32 <= kPool
     np += 32;
     __syncwarp();
   }
@@ -419,10 +455,11 @@ __device__ __forceinline__ bool pool_take(const Ctx& c, AsyncWS& w, int n) {
 }
 
 // Puts n slots s[0, n) back into the pool; what does not fit goes to the pending list.
-__device__ __forceinline__ void pool_give(const Ctx& c, AsyncWS& w, const uint32_t* s, int n) {
+template <class W>
+__device__ __forceinline__ void pool_give(const Ctx& c, W& w, const uint32_t* s, int n) {
   const int lane = threadIdx.x & 31;
   const int np = w.np;
-  const int keep = min(n, kAPool - np);
+  const int keep = min(n, W::kPool - np);
   for (int i = lane; i < keep; i += 32) w.pool[np + i] = s[i];
   if (n > keep) {
     unsigned long long pb = 0;
@@ -439,7 +476,8 @@ __device__ __forceinline__ void pool_give(const Ctx& c, AsyncWS& w, const uint32
 }
 
 // One attempt at inserting p (steps 1-5). w.hint is the warp's last ball, updated on success.
-__device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lock, uint32_t me, uint32_t p,
+template <class W>
+__device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, uint32_t me, uint32_t p,
                                           const InsertLog& lg) {
   const int lane = threadIdx.x & 31;
   const PtF FP = load_ptf(c.ptf, p);
@@ -493,12 +531,12 @@ __device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lo
     if (nx > 0 && !pool_take(c, w, nx)) return kALost;
     // 3. lock C, A and the extra slots
     const int nl = nc + na + nx;
-    unsigned held = 0;
+    typename W::Held held = 0;
     bool ok = true;
     for (int k = 0; lane + 32 * k < nl; ++k) {
       const uint32_t s = lock_entry(w, lane + 32 * k, nc, na, nx);
       if (s == kNone) continue;
-      if (atomicCAS(&lock[s], 0u, me) == 0u) held |= 1u << k;
+      if (atomicCAS(&lock[s], 0u, me) == 0u) held |= (typename W::Held)1 << k;
       else ok = false;
     }
     if (!__all_sync(kFull, ok)) {
@@ -523,22 +561,53 @@ __device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lo
     // 5. the ball: cavity slots first, then the extra slots
     for (int i = lane; i < nb; i += 32) w.slot[i] = i < reuse ? w.cl[i] : w.ex[i - reuse];
     w.vkey[lane] = kNoVertex;
+    if constexpr (!W::kTable) {
+      for (uint32_t i = lane; i < W::kEdgeN; i += 32) {
+        w.ekey[i] = ~0ull;
+        w.eval[i] = kNone;
+      }
+    }
     __syncwarp();
+    // record every internal facet: facet a of new tetrahedron i holds the boundary edge b -> c
     bool vfail = false;
     for (int i = lane; i < nb; i += 32) {
       const int ci = w.bl_ci[i], f = w.bl_f[i];
       uint4 v = w.cr[ci].v;
       set4(v, f, p);
-      int a, b, cc;
-      after_pos(f, a, b, cc);
-      const int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
-      if (la < 0 || lb < 0 || lc < 0) {
-        vfail = true;
-        continue;
+      int pos[3];
+      after_pos(f, pos[0], pos[1], pos[2]);
+      if constexpr (W::kTable) {
+        const int la = vslot(w.vkey, get4(v, pos[0])), lb = vslot(w.vkey, get4(v, pos[1])),
+                  lc = vslot(w.vkey, get4(v, pos[2]));
+        if (la < 0 || lb < 0 || lc < 0) {
+          vfail = true;
+          continue;
+        }
+        w.tab[lb * 32 + lc] = (uint16_t)((i << 2) | pos[0]);
+        w.tab[lc * 32 + la] = (uint16_t)((i << 2) | pos[1]);
+        w.tab[la * 32 + lb] = (uint16_t)((i << 2) | pos[2]);
+      } else {
+        for (int k = 0; k < 3; ++k) {
+          const uint32_t x = get4(v, pos[(k + 1) % 3]), y = get4(v, pos[(k + 2) % 3]);
+          const unsigned long long key = ((unsigned long long)min(x, y) << 32) | max(x, y);
+          uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (W::kEdgeN - 1), sl = kNone;
+#pragma unroll 1
+          for (uint32_t probe = 0; probe < W::kEdgeN; ++probe) {
+            const unsigned long long old = atomicCAS(&w.ekey[h], ~0ull, key);
+            if (old == ~0ull || old == key) {
+              sl = h;
+              break;
+            }
+            h = (h + 1) & (W::kEdgeN - 1);
+          }
+          if (sl == kNone) {
+            vfail = true;
+            break;
+          }
+          w.hslot[3 * i + k] = sl;
+          w.hold[3 * i + k] = atomicExch(&w.eval[sl], (uint32_t)((i << 2) | pos[k]));
+        }
       }
-      w.tab[lb * 32 + lc] = (uint16_t)((i << 2) | a);
-      w.tab[lc * 32 + la] = (uint16_t)((i << 2) | b);
-      w.tab[la * 32 + lb] = (uint16_t)((i << 2) | cc);
     }
     __syncwarp();
     // every internal facet was recorded by its two sides (the cavity was verified under the
@@ -551,8 +620,22 @@ __device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lo
       set4(v, f, p);
       int a, b, cc;
       after_pos(f, a, b, cc);
-      const int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
-      const uint32_t ea = vld(&w.tab[lc * 32 + lb]), eb = vld(&w.tab[la * 32 + lc]), ec = vld(&w.tab[lb * 32 + la]);
+      uint32_t ea, eb, ec;
+      if constexpr (W::kTable) {
+        const int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
+        ea = vld(&w.tab[lc * 32 + lb]);
+        eb = vld(&w.tab[la * 32 + lc]);
+        ec = vld(&w.tab[lb * 32 + la]);
+      } else {
+        uint32_t e3[3];
+        for (int k = 0; k < 3; ++k) {
+          const uint32_t old = w.hold[3 * i + k];
+          e3[k] = old != kNone ? old : vld(&w.eval[w.hslot[3 * i + k]]);
+        }
+        ea = e3[0];
+        eb = e3[1];
+        ec = e3[2];
+      }
       if ((ea >> 2) >= (uint32_t)nb || (eb >> 2) >= (uint32_t)nb || (ec >> 2) >= (uint32_t)nb ||
           (ea >> 2) == (uint32_t)i || (eb >> 2) == (uint32_t)i || (ec >> 2) == (uint32_t)i) {
         bad = true;
@@ -599,7 +682,7 @@ __device__ __forceinline__ int try_insert(const Ctx& c, AsyncWS& w, uint32_t* lo
       if ((w.cnt[0] & 63u) == 0) c.st->anchor = s0;
       log_outcome(lg, p, kCandInserted, nc);
       w.hint = s0;
-      w.bn = nb < 32 ? nb : 32;
+      w.bn = W::kTable ? (nb < 32 ? nb : 32) : 0;
       w.cnt[0] += 1;
       w.cnt[3] += nc;
       w.cnt[4] += nb;
@@ -619,17 +702,56 @@ __device__ __forceinline__ void to_queue(const AsyncIO& io, const Ctx& c, int q,
   out[b] = p;
 }
 
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO io, uint32_t* lock,
-                                                               const uint8_t* __restrict__ vflag, InsertLog lg) {
-  __shared__ AsyncWS s_ws[kAW];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  AsyncWS& w = s_ws[wid];
-  const uint32_t seg = blockIdx.x * kAW + wid;
-  if (seg >= io.W) return;
-  const uint32_t me = seg + 1;
-  const uint64_t b0 = (uint64_t)seg * io.L;
-  const uint64_t e0 = b0 + io.L < io.m ? b0 + io.L : io.m;
+// A cavity too large for the warp's shared-memory workspace: the same insertion again in a
+// global-memory workspace borrowed from the launch's pool (tried at a few places, never waited
+// for). Returns kABig when none is free or the cavity exceeds it too. The borrowed workspace's
+// counters, spare slots and ball hint come back to the warp's own.
+template <class W>
+__device__ __forceinline__ int try_insert_large(const Ctx& c, const AsyncIO& io, W& w, uint32_t* lock, uint32_t me,
+                                                uint32_t p, const InsertLog& lg) {
+  if (!io.big_ws || io.big_n == 0) return kABig;
+  const int lane = threadIdx.x & 31;
+  int k = -1;
+  if (lane == 0)
+    for (int t = 0; t < 8 && k < 0; ++t) {
+      const uint32_t cand = (me * 0x9E3779B1u + (uint32_t)t * 0x85EBCA6Bu) % io.big_n;
+      if (atomicCAS(&io.big_busy[cand], 0u, 1u) == 0u) k = (int)cand;
+    }
+  k = __shfl_sync(kFull, k, 0);
+  if (k < 0) return kABig;
+  LargeWS& L = static_cast<LargeWS*>(io.big_ws)[k];
+  if (lane == 0) {
+    L.fa = w.fa;
+    L.bump = w.bump;
+    L.np = 0;
+    L.bn = 0;
+    L.hint = w.hint;
+    for (int q = 0; q < 8; ++q) L.cnt[q] = 0;
+  }
+  __syncwarp();
+  const int r = try_insert(c, L, lock, me, p, lg);
+  pool_give(c, w, L.pool, L.np);
+  if (lane == 0) {
+    w.cnt[0] += L.cnt[0];
+    w.cnt[3] += L.cnt[3];
+    w.cnt[4] += L.cnt[4];
+    w.cnt[5] += L.cnt[5];
+    w.cnt[6] += L.cnt[6];
+    if (r == kAInserted) w.hint = L.hint;
+    w.bn = 0;
+    __threadfence();
+    atomicExch(&io.big_busy[k], 0u);
+  }
+  __syncwarp();
+  return r;
+}
+
+// One warp's work: segment [b0, e0) of io's list in order, deferred points retried after later
+// insertions, then what is left handed on, unused slots returned and counters flushed.
+template <class W>
+__device__ __forceinline__ void run_segment(const Ctx& c, const AsyncIO& io, W& w, uint32_t* lock, uint32_t me,
+                                            uint64_t b0, uint64_t e0, const uint8_t* vflag, const InsertLog& lg) {
+  const int lane = threadIdx.x & 31;
   if (lane == 0) {
     w.fa = __ldcg(&c.st->free_avail);
     w.bump = __ldcg(&c.st->bump);
@@ -660,7 +782,10 @@ __global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO i
       break;
     }
     if (lane == 0) w.cnt[2] += 1;
-    const int r = try_insert(c, w, lock, me, p, lg);
+    int r = try_insert(c, w, lock, me, p, lg);
+    if constexpr (W::kTable) {
+      if (r == kABig) r = try_insert_large(c, io, w, lock, me, p, lg);
+    }
     // a raised error stops the launch; read every 16 points for the same reason as the anchor
     unsigned err = 0;
     if (lane == 0 && (w.cnt[2] & 15u) == 0) err = __ldcg(&c.st->error);
@@ -708,6 +833,30 @@ __global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO i
     for (int k = 0; k < 8; ++k)
       if (w.cnt[k]) atomicAdd(dst[k], (unsigned long long)w.cnt[k]);
   }
+}
+
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO io, uint32_t* lock,
+                                                               const uint8_t* __restrict__ vflag, InsertLog lg) {
+  __shared__ SmallWS s_ws[kAW];
+  const int wid = threadIdx.x >> 5;
+  const uint32_t seg = blockIdx.x * kAW + wid;
+  if (seg >= io.W) return;
+  const uint64_t b0 = (uint64_t)seg * io.L;
+  const uint64_t e0 = b0 + io.L < io.m ? b0 + io.L : io.m;
+  run_segment(c, io, s_ws[wid], lock, seg + 1, b0, e0, vflag, lg);
+}
+
+// Large cavities (beyond the shared-memory workspaces): the same insertion with each warp's
+// workspace in global memory. Owner words are per warp of the launch, and this kernel never
+// runs beside k_async, so warp numbers may repeat across the two.
+__global__ void __launch_bounds__(128) k_async_big(Ctx c, AsyncIO io, uint32_t* lock, const uint8_t* __restrict__ vflag,
+                                                  InsertLog lg, LargeWS* ws) {
+  const uint32_t seg = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (seg >= io.W) return;
+  const uint64_t b0 = (uint64_t)seg * io.L;
+  const uint64_t e0 = b0 + io.L < io.m ? b0 + io.L : io.m;
+  run_segment(c, io, ws[seg], lock, seg + 1, b0, e0, vflag, lg);
 }
 
 // Folds the allocator of the launch into the free list, as a round close does
@@ -769,6 +918,21 @@ int async_launch(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t*
     case 6: k_async<6><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
     default: k_async<8><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
   }
+  k_async_close_copy<<<152, 256, 0, s>>>(cc);
+  k_async_close_state<<<1, 1, 0, s>>>(cc);
+  g_kernel_launches += 3;
+  return cudaPeekAtLastError() == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
+size_t async_big_ws_bytes() { return sizeof(LargeWS); }
+
+int async_launch_big(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t* vflag, const InsertLog& lg,
+                     void* ws, cudaStream_t s) {
+  if (io.W == 0 || io.m == 0) return DT_OK;
+  Ctx cc = c;
+  cc.coherent = 1;
+  cc.max_walk = io.max_walk;
+  k_async_big<<<(io.W + 3) / 4, 128, 0, s>>>(cc, io, lock, vflag, lg, static_cast<LargeWS*>(ws));
   k_async_close_copy<<<152, 256, 0, s>>>(cc);
   k_async_close_state<<<1, 1, 0, s>>>(cc);
   g_kernel_launches += 3;

@@ -22,6 +22,8 @@ constexpr int kCavWarps = 4;  // candidates per block of the cavity kernel (4 me
 constexpr int kInsWarps = 8;  // candidates per block of the ball kernel
 constexpr uint32_t kDefaultWalk = 48;          // walk steps per pass (a longer walk resumes next pass)
 constexpr uint32_t kAsyncWalk = 4096;          // walk steps per attempt of the asynchronous engine
+constexpr uint32_t kAsyncBigWarps = 512;       // warps (global-memory workspaces) of its large-cavity kernel
+constexpr uint32_t kAsyncBorrow = 256;         // large-cavity workspaces the main kernel's warps may borrow
 constexpr uint64_t kLongWalkBelow = 8192;      // retry lists shorter than this walk up to
 constexpr uint32_t kLongWalkSteps = 1u << 14;  // this many steps per pass
 constexpr uint32_t kScratchStride = kCMax + kFMax;
@@ -821,6 +823,9 @@ struct dt_handle {
   double alpha_async = 0.02; // concurrent insertions (warps) per mesh vertex of the asynchronous engine
   uint64_t async_min_retry = 2048; // retry lists shorter than this use the round-based engine
   uint64_t async_warps = 0;        // cap on the asynchronous engine's warps (0: all that fit)
+  char* async_big_ws = nullptr;    // global-memory workspaces of the asynchronous large-cavity kernel
+  char* async_borrow_ws = nullptr; // workspaces the main asynchronous kernel's warps borrow
+  unsigned int* async_borrow_busy = nullptr;
   bool big_smem = true;    // large cavities try the shared-memory workspaces first
   int big_smem_skip = 0;   // passes left that go straight to the global-memory tier
   uint32_t* wlist = nullptr;
@@ -955,7 +960,9 @@ uint64_t device_bytes(const dt_handle* h) {
     b += (uint64_t)h->Rmax * (5 * 4 + (uint64_t)kScratchStride * 4);
     b += h->bigstride * kBigR + (uint64_t)kBigR * (kMedCN + kMedFN) * 4 + h->ctastride * kCtaWarps;
   }
-  b += h->cap_q * 4 * 5 + h->cap_w * 4;
+  b += h->cap_q * 4 * kNumQueues + h->cap_w * 4;
+  if (h->async_big_ws) b += (uint64_t)kAsyncBigWarps * async_big_ws_bytes();
+  if (h->async_borrow_ws) b += (uint64_t)kAsyncBorrow * (async_big_ws_bytes() + 4);
   if (h->hugemem) b += carve(nullptr, 4 * h->huge_c, h->huge_c, h->huge_c, 4 * h->huge_c, nullptr);
   b += h->cap_log * 3 + h->cap_feat * (8 + 2) * 4 + h->cap_risky * 2 + h->cap_cells * 4;
   b += h->cap_bpts * 32 + h->cap_bws + h->cap_bstates * sizeof(DevState);
@@ -1199,6 +1206,38 @@ int run_big(dt_handle* h, const Ctx& c) {
   return DT_OK;
 }
 
+// Large cavities of an asynchronous pass: the asynchronous kernel with global-memory
+// workspaces, again on its losers while that makes progress; whatever is left (and cavities
+// beyond those workspaces) goes through the large-cavity rounds and the serial path.
+int run_big_async(dt_handle* h, const Ctx& c) {
+  uint64_t nbig = h->st_host->q[kQBig];
+  if (nbig > 0 && !h->async_big_ws &&
+      cudaMalloc(&h->async_big_ws, (size_t)kAsyncBigWarps * async_big_ws_bytes()) != cudaSuccess)
+    return DT_ENOMEM;
+  for (int iter = 0; nbig > 0 && iter < 8; ++iter) {
+    int rc = set_queue_lengths(h, {kQBig2});
+    if (rc != DT_OK) return rc;
+    uint64_t W = std::min<uint64_t>(nbig, kAsyncBigWarps);
+    const uint64_t L = (nbig + W - 1) / W;
+    W = (nbig + L - 1) / L;
+    AsyncIO io{h->queue[kQBig], 0, nbig, L, (uint32_t)W, h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kAsyncWalk,
+               h->queue[kQBig2], kQBig2, h->queue[kQHuge], kQHuge, h->queue[kQExact], kQExact,
+               nullptr, nullptr, 0};
+    if ((rc = async_launch_big(c, io, h->lock, h->vflag, make_log(h), h->async_big_ws, h->stream)) != DT_OK)
+      return rc;
+    h->stats.n_async++;
+    if ((rc = sync_state(h)) != DT_OK) return rc;
+    const uint64_t left = h->st_host->q[kQBig2];
+    std::swap(h->queue[kQBig], h->queue[kQBig2]);
+    h->st_host->q[kQBig] = left;
+    if (cudaMemcpyAsync(&h->st->q[kQBig], &left, 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return DT_ECUDA;
+    if (left >= nbig) break;  // no progress: the rounds below settle the rest
+    nbig = left;
+  }
+  return run_big(h, c);
+}
+
 // One pass: rounds over q[0..m) (or the vertex range qbase + [0, m)) split into R segments of
 // length L (segment s offers q[s*L + j] in round j), then the large cavities of the pass.
 int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next,
@@ -1215,8 +1254,15 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   int rc = reset_next ? set_queue_lengths(h, {kQNext, kQBig, kQHuge}) : set_queue_lengths(h, {kQBig, kQHuge});
   if (rc != DT_OK) return rc;
   if ((rc = set_queue_lengths(h, {kQExact})) != DT_OK) return rc;
+  if (!h->async_borrow_ws) {
+    if (cudaMalloc(&h->async_borrow_ws, (size_t)kAsyncBorrow * async_big_ws_bytes()) != cudaSuccess ||
+        cudaMalloc(&h->async_borrow_busy, kAsyncBorrow * sizeof(unsigned int)) != cudaSuccess)
+      return DT_ENOMEM;
+    cudaMemsetAsync(h->async_borrow_busy, 0, kAsyncBorrow * sizeof(unsigned int), h->stream);
+  }
   AsyncIO io{q, qbase, m, L, (uint32_t)W, h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kAsyncWalk,
-             h->queue[kQNext], kQNext, h->queue[kQBig], kQBig, h->queue[kQExact], kQExact};
+             h->queue[kQNext], kQNext, h->queue[kQBig], kQBig, h->queue[kQExact], kQExact,
+             h->async_borrow_ws, h->async_borrow_busy, kAsyncBorrow};
   const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0;
   if (prof) cudaEventRecord(h->ev[3], h->stream);
   if ((rc = async_launch(c, io, h->lock, h->vflag, make_log(h), h->stream)) != DT_OK) return rc;
@@ -1231,7 +1277,7 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   }
   // large cavities now (deferring them to the end of the BRIO round was measured slower: they
   // then meet each other, 592 instead of 395 rounds per 1e7 uniform step)
-  if ((rc = run_big(h, c)) != DT_OK) return rc;
+  if ((rc = run_big_async(h, c)) != DT_OK) return rc;
   // points whose predicates the asynchronous engine's FP32 stage could not decide: one
   // round-based pass with the full predicate cascade (its losers join the next pass's list)
   const uint64_t ne = h->st_host->q[kQExact];
@@ -2326,6 +2372,9 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->tets);
   cudaFree(h->claim);
   cudaFree(h->lock);
+  cudaFree(h->async_big_ws);
+  cudaFree(h->async_borrow_ws);
+  cudaFree(h->async_borrow_busy);
   cudaFree(h->freelist);
   cudaFree(h->pending);
   cudaFree(h->cell_hint);

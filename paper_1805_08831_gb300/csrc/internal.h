@@ -142,6 +142,9 @@ struct AsyncIO {
   int big_q;
   uint32_t* exact_out;  // predicates the FP32 stage cannot decide: the round-based engine's
   int exact_q;
+  void* big_ws;         // global-memory workspaces a warp may borrow for a large cavity (or null)
+  unsigned int* big_busy;  // one word per workspace: 0 free, 1 borrowed
+  uint32_t big_n;       // workspaces
 };
 // Enqueues the asynchronous insertion of one pass and the close of its allocator. lock: one
 // word per tetrahedron slot, all zero before and after.
@@ -149,6 +152,12 @@ int async_launch(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t*
                  cudaStream_t s);
 // Warps of the asynchronous kernel that can be resident on the current device at once.
 int async_max_warps();
+// The same insertion for cavities beyond the main kernel's shared-memory workspaces: io.W warps
+// with one global-memory workspace of async_big_ws_bytes() each at ws (device). Points whose
+// cavities exceed even these go to io.big_out.
+size_t async_big_ws_bytes();
+int async_launch_big(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t* vflag, const InsertLog& lg,
+                     void* ws, cudaStream_t s);
 
 // ---------------------------------------------------------------- batch.cu (dt_batch)
 size_t batch_ws_stride();       // bytes of one warp's workspace

@@ -161,16 +161,20 @@ __device__ __forceinline__ int inside_async(const Ctx& c, const uint4& v, const 
   return insphere_f(A, B, C, D, FP, c.eta);
 }
 
-// Visibility walk (Section 2.1, ghost rules of Section 2.6) on unlocked reads, by one lane. A
-// record that is being rewritten may be read half old, half new: such reads end the walk with
-// kARestart (or it runs into its step bound); nothing is trusted before step 4 re-reads it
-// under a lock.
+// Visibility walk (Section 2.1, ghost rules of Section 2.6) on unlocked reads. Lanes 0-3 test
+// the four facets of the current tetrahedron at once (lane i: p against the facet opposite
+// vertex i), and the walk leaves through the first facet p sees, in an order that turns with
+// the steps. A record that is being rewritten may be read half old, half new: such reads end
+// the walk with kARestart (or it runs into its step bound); nothing is trusted before step 4
+// re-reads it under a lock. Called by the whole warp; the result is uniform.
 __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& FP, uint32_t start, uint32_t salt,
                                           uint32_t max_steps, uint32_t* t_out, uint32_t* steps_out) {
+  const int lane = threadIdx.x & 31;
   uint32_t t = start;
   Tet T;
-  int hops = 0;
   *steps_out = 0;
+  *t_out = kNone;
+  int hops = 0;
   for (;;) {
     if (t == kNone || t >= c.ntets) t = __ldcg(&c.st->anchor);
     if (t >= c.ntets) return kARestart;
@@ -189,39 +193,37 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
   uint32_t prev = kNone, steps = 0;
   for (;;) {
     if (ghost_pos(T.v) >= 0) break;
-    const PtF F0 = load_ptf(c.ptf, T.v.x), F1 = load_ptf(c.ptf, T.v.y), F2 = load_ptf(c.ptf, T.v.z),
-              F3 = load_ptf(c.ptf, T.v.w);
-    int exit = -1;
-    const int s0 = (salt + steps) & 3;
-#pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-      const int i = (s0 + k) & 3;
-      if ((get4(T.n, i) >> 2) == prev) continue;
-      const int o = orient_with_p(c, i, FP, F0, F1, F2, F3);
-      if (o == 0) return kAExact;
-      if (o < 0) {
-        exit = i;
-        break;
-      }
+    // lane i < 4: orientation of p against the facet opposite vertex i (0: undecided)
+    int o = 1;
+    if (lane < 4) {
+      const PtF F0 = load_ptf(c.ptf, T.v.x), F1 = load_ptf(c.ptf, T.v.y), F2 = load_ptf(c.ptf, T.v.z),
+                F3 = load_ptf(c.ptf, T.v.w);
+      o = (get4(T.n, lane) >> 2) == prev ? 1 : orient_with_p(c, lane, FP, F0, F1, F2, F3);
     }
-    if (exit < 0) {
+    const unsigned sees = __ballot_sync(kFull, lane < 4 && o < 0) & 0xFu;
+    if (__ballot_sync(kFull, lane < 4 && o == 0) & 0xFu) return kAExact;
+    if (sees == 0) {
+      // p is inside (or on) this tetrahedron: a vertex equal to p would be a duplicate
       bool dup = false;
-      if (same_f(F0, FP) || same_f(F1, FP) || same_f(F2, FP) || same_f(F3, FP)) {
-        Pt P = load_pt(c.pts, p);
-        for (int k = 0; k < 4; ++k) {
-          Pt V = load_pt(c.pts, get4(T.v, k));
-          dup = dup || (V.x == P.x && V.y == P.y && V.z == P.z);
+      if (lane < 4) {
+        const PtF V = load_ptf(c.ptf, get4(T.v, lane));
+        if (same_f(V, FP)) {
+          const Pt P = load_pt(c.pts, p), Q = load_pt(c.pts, get4(T.v, lane));
+          dup = Q.x == P.x && Q.y == P.y && Q.z == P.z;
         }
       }
       *t_out = t;
       *steps_out = steps;
-      return dup ? kADup : kAInserted;
+      return __any_sync(kFull, dup) ? kADup : kAInserted;
     }
     if (steps >= max_steps) {
       *t_out = t;
       *steps_out = steps;
       return kAWalkLimit;
     }
+    // the first facet p sees, starting from a position that turns with the steps
+    const unsigned rot = ((sees | (sees << 4)) >> ((salt + steps) & 3)) & 0xFu;
+    const int exit = (__ffs(rot) - 1 + (int)((salt + steps) & 3)) & 3;
     prev = t;
     t = get4(T.n, exit) >> 2;
     T = ld_tet(c.tets, t);
@@ -497,8 +499,8 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
       const unsigned m = __ballot_sync(kFull, in);
       if (m) t0 = w.slot[__ffs(m) - 1];
     }
-    if (t0 == kNone && lane == 0) {
-      uint32_t start = attempt == 0 ? w.hint : c.point_hint[p];
+    if (t0 == kNone) {
+      uint32_t start = attempt == 0 ? w.hint : kNone;
       if (start == kNone) start = c.point_hint[p];
       if (start == kNone) {
         uint32_t f, g;
@@ -506,13 +508,14 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
         start = c.cell_hint[f];
         if (start == kNone) start = c.cell_hint2[g];
       }
+      start = __shfl_sync(kFull, start, 0);
       uint32_t steps = 0;
       ws = walk_async(c, p, FP, start, p * 0x9E3779B1u >> 30, c.max_walk, &t0, &steps);
-      if (t0 != kNone && t0 < c.ntets) c.point_hint[p] = t0;
-      w.cnt[5] += steps;
+      if (lane == 0) {
+        if (t0 != kNone && t0 < c.ntets) c.point_hint[p] = t0;
+        w.cnt[5] += steps;
+      }
     }
-    ws = __shfl_sync(kFull, ws, 0);
-    t0 = __shfl_sync(kFull, t0, 0);
     if (lane == 0) w.bn = 0;  // used once
     if (ws == kADup || ws == kAWalkLimit || ws == kAExact) return ws;
     if (ws == kARestart) {
@@ -705,10 +708,11 @@ __device__ __forceinline__ void to_queue(const AsyncIO& io, const Ctx& c, int q,
 // A cavity too large for the warp's shared-memory workspace: the same insertion again in a
 // global-memory workspace borrowed from the launch's pool (tried at a few places, never waited
 // for). Returns kABig when none is free or the cavity exceeds it too. The borrowed workspace's
-// counters, spare slots and ball hint come back to the warp's own.
+// counters, spare slots and ball hint come back to the warp's own. Out of line: it runs for
+// about one point in 1500, and inlined it would double the kernel's instruction footprint.
 template <class W>
-__device__ __forceinline__ int try_insert_large(const Ctx& c, const AsyncIO& io, W& w, uint32_t* lock, uint32_t me,
-                                                uint32_t p, const InsertLog& lg) {
+__device__ __noinline__ int try_insert_large(const Ctx& c, const AsyncIO& io, W& w, uint32_t* lock, uint32_t me,
+                                             uint32_t p, const InsertLog& lg) {
   if (!io.big_ws || io.big_n == 0) return kABig;
   const int lane = threadIdx.x & 31;
   int k = -1;

@@ -823,6 +823,7 @@ struct dt_handle {
   double alpha_async = 0.02; // concurrent insertions (warps) per mesh vertex of the asynchronous engine
   uint64_t async_min_retry = 2048; // retry lists shorter than this use the round-based engine
   uint64_t async_warps = 0;        // cap on the asynchronous engine's warps (0: all that fit)
+  bool async_off = false;          // this call's inputs defeat the asynchronous engine's FP32 stage
   char* async_big_ws = nullptr;    // global-memory workspaces of the asynchronous large-cavity kernel
   char* async_borrow_ws = nullptr; // workspaces the main asynchronous kernel's warps borrow
   unsigned int* async_borrow_busy = nullptr;
@@ -1283,12 +1284,16 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   const uint64_t ne = h->st_host->q[kQExact];
   if (ne == 0) return DT_OK;
   h->stats.n_exact_handoff += ne;
+  // when the FP32 stage cannot decide for a fifth of a pass's points (near-degenerate inputs:
+  // lattices, co-spherical surfaces, refinement centres), the work it did was mostly wasted:
+  // the rest of this call runs on the round-based engine
+  if (5 * ne > m) h->async_off = true;
   return run_pass(h, c, h->queue[kQExact], 0, ne, false, 1.f, true);
 }
 
 int run_pass(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase, uint64_t m, bool reset_next,
              float alpha_scale, bool rounds_only) {
-  if (h->use_async && !rounds_only && (!reset_next || m >= h->async_min_retry))
+  if (h->use_async && !h->async_off && !rounds_only && (!reset_next || m >= h->async_min_retry))
     return run_pass_async(h, c, q, qbase, m, reset_next);
   uint64_t& kind_rounds = reset_next ? h->stats.n_rounds_retry : h->stats.n_rounds_wave;
   uint64_t mesh = h->st_host->n_inserted;
@@ -1464,6 +1469,7 @@ int schedule_learned(dt_handle* h, uint64_t n);
 
 int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
   if (n == 0) return h->has_mesh ? DT_OK : DT_EDEGENERATE;
+  h->async_off = false;
   if (h->n_pts + n >= 0xFFFFFFF0ull) return DT_EINVAL;
   cudaStream_t s = h->stream;
   cudaEventRecord(h->ev[0], s);

@@ -846,8 +846,14 @@ __global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO i
   const int wid = threadIdx.x >> 5;
   const uint32_t seg = blockIdx.x * kAW + wid;
   if (seg >= io.W) return;
-  const uint64_t b0 = (uint64_t)seg * io.L;
-  const uint64_t e0 = b0 + io.L < io.m ? b0 + io.L : io.m;
+  uint64_t b0, e0;
+  if (io.bounds) {  // segments of equal predicted work (the learned schedule)
+    b0 = io.bounds[seg];
+    e0 = io.bounds[seg + 1];
+  } else {
+    b0 = (uint64_t)seg * io.L;
+    e0 = b0 + io.L < io.m ? b0 + io.L : io.m;
+  }
   run_segment(c, io, s_ws[wid], lock, seg + 1, b0, e0, vflag, lg);
 }
 

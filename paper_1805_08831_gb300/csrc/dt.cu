@@ -749,6 +749,37 @@ __global__ void k_risky(const float* __restrict__ pred, uint64_t n, uint32_t vb,
 }
 
 // Histogram of the 2 x (wave) sub-wave keys of a BRIO round.
+// Predicted insertion work of each vertex (learned schedule): a fixed part for the walk, the
+// locks and the ball, plus a quarter of the predicted cavity size |C| = 2^out0 - 1.
+__global__ void k_work(const float* __restrict__ pred, uint64_t n, uint32_t vb, uint8_t* wcost) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n; s += (uint64_t)gridDim.x * blockDim.x) {
+    const float c = exp2f(fminf(fmaxf(pred[2 * s], 0.f), 7.f)) - 1.f;
+    wcost[vb + s] = (uint8_t)(4.f + rintf(c * 0.25f));
+  }
+}
+
+__global__ void k_seg_cost(const uint32_t* __restrict__ q, uint32_t qbase, uint64_t m, const uint8_t* __restrict__ wcost,
+                           uint32_t* out) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = wcost[q ? q[i] : qbase + (uint32_t)i];
+}
+
+// bounds[w] = the first list position whose exclusive prefix of work reaches w / W of the total.
+__global__ void k_seg_bounds(const uint32_t* __restrict__ prefix, const uint32_t* __restrict__ q, uint32_t qbase,
+                             uint64_t m, const uint8_t* __restrict__ wcost, uint32_t W, uint32_t* bounds) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w > W) return;
+  const uint64_t total = (uint64_t)prefix[m - 1] + wcost[q ? q[m - 1] : qbase + (uint32_t)(m - 1)];
+  const uint64_t target = total * w / W;
+  uint64_t lo = 0, hi = m;  // first i in [0, m] with prefix[i] >= target (prefix[m] = total)
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) / 2;
+    if ((uint64_t)prefix[mid] >= target) hi = mid;
+    else lo = mid + 1;
+  }
+  bounds[w] = (uint32_t)(w == W ? m : lo);
+}
+
 __global__ void k_key_hist(const uint64_t* __restrict__ keys, uint64_t m, uint32_t* hist) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
     atomicAdd(&hist[keys[i]], 1u);
@@ -824,6 +855,12 @@ struct dt_handle {
   uint64_t async_min_retry = 2048; // retry lists shorter than this use the round-based engine
   uint64_t async_warps = 0;        // cap on the asynchronous engine's warps (0: all that fit)
   bool async_off = false;          // this call's inputs defeat the asynchronous engine's FP32 stage
+  uint8_t* wcost = nullptr;        // learned schedule: predicted insertion work per vertex
+  bool wcost_ready = false;
+  uint32_t* seg_prefix = nullptr;  // prefix sums of a pass's predicted work
+  uint64_t cap_seg = 0;
+  uint32_t* seg_bounds = nullptr;  // the pass's segment starts
+  uint64_t cap_wcost = 0;
   char* async_big_ws = nullptr;    // global-memory workspaces of the asynchronous large-cavity kernel
   char* async_borrow_ws = nullptr; // workspaces the main asynchronous kernel's warps borrow
   unsigned int* async_borrow_busy = nullptr;
@@ -1223,7 +1260,7 @@ int run_big_async(dt_handle* h, const Ctx& c) {
     W = (nbig + L - 1) / L;
     AsyncIO io{h->queue[kQBig], 0, nbig, L, (uint32_t)W, h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kAsyncWalk,
                h->queue[kQBig2], kQBig2, h->queue[kQHuge], kQHuge, h->queue[kQExact], kQExact,
-               nullptr, nullptr, 0};
+               nullptr, nullptr, nullptr, 0};
     if ((rc = async_launch_big(c, io, h->lock, h->vflag, make_log(h), h->async_big_ws, h->stream)) != DT_OK)
       return rc;
     h->stats.n_async++;
@@ -1255,6 +1292,24 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   int rc = reset_next ? set_queue_lengths(h, {kQNext, kQBig, kQHuge}) : set_queue_lengths(h, {kQBig, kQHuge});
   if (rc != DT_OK) return rc;
   if ((rc = set_queue_lengths(h, {kQExact})) != DT_OK) return rc;
+  // learned schedule: segments of equal predicted work (a fixed part plus the predicted cavity)
+  const uint32_t* seg_bounds = nullptr;
+  if (h->wcost_ready && h->cfg.schedule == DT_SCHED_LEARNED) {
+    if (m > h->cap_seg) {
+      cudaFree(h->seg_prefix);
+      h->seg_prefix = nullptr;
+      if (cudaMalloc(&h->seg_prefix, m * 4) != cudaSuccess) return DT_ENOMEM;
+      h->cap_seg = m;
+    }
+    if (!h->seg_bounds && cudaMalloc(&h->seg_bounds, ((size_t)async_max_warps() + 1) * 4) != cudaSuccess)
+      return DT_ENOMEM;
+    k_seg_cost<<<grid_for(m, 256), 256, 0, h->stream>>>(q, qbase, m, h->wcost, h->seg_prefix);
+    prefix_sum_exclusive(h->seg_prefix, m, h->ows.hist, h->stream);
+    k_seg_bounds<<<grid_for(W + 1, 256), 256, 0, h->stream>>>(h->seg_prefix, q, qbase, m, h->wcost, (uint32_t)W,
+                                                               h->seg_bounds);
+    g_kernel_launches += 2;
+    seg_bounds = h->seg_bounds;
+  }
   if (!h->async_borrow_ws) {
     if (cudaMalloc(&h->async_borrow_ws, (size_t)kAsyncBorrow * async_big_ws_bytes()) != cudaSuccess ||
         cudaMalloc(&h->async_borrow_busy, kAsyncBorrow * sizeof(unsigned int)) != cudaSuccess)
@@ -1263,7 +1318,7 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   }
   AsyncIO io{q, qbase, m, L, (uint32_t)W, h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kAsyncWalk,
              h->queue[kQNext], kQNext, h->queue[kQBig], kQBig, h->queue[kQExact], kQExact,
-             h->async_borrow_ws, h->async_borrow_busy, kAsyncBorrow};
+             seg_bounds, h->async_borrow_ws, h->async_borrow_busy, kAsyncBorrow};
   const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0;
   if (prof) cudaEventRecord(h->ev[3], h->stream);
   if ((rc = async_launch(c, io, h->lock, h->vflag, make_log(h), h->stream)) != DT_OK) return rc;
@@ -1486,6 +1541,7 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n) {
   h->last_base = base;
   h->risky_ready = false;
   h->prank_ready = false;
+  h->wcost_ready = false;
   if (h->cfg.flags & DT_FLAG_LOG) {
     if (h->cap_pts > h->cap_log) {
       uint16_t* a = nullptr;
@@ -2004,7 +2060,6 @@ int schedule_learned(dt_handle* h, uint64_t n) {
     }
     cudaStreamSynchronize(h->stream);
     cudaFree(h->risky);
-  cudaFree(h->prank);
     cudaFree(h->prank);
     h->risky = r;
     h->prank = k;
@@ -2015,6 +2070,18 @@ int schedule_learned(dt_handle* h, uint64_t n) {
                                                     h->use_defer ? h->risky_logit : 1e30f, h->rank_scale, h->risky,
                                                     h->prank);
   ++g_kernel_launches;
+  if (h->last_base + n > h->cap_wcost) {
+    uint8_t* wc = nullptr;
+    if (cudaMalloc(&wc, h->cap_pts) != cudaSuccess) return DT_ENOMEM;
+    if (h->wcost && h->last_base) cudaMemcpyAsync(wc, h->wcost, h->last_base, cudaMemcpyDeviceToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->wcost);
+    h->wcost = wc;
+    h->cap_wcost = h->cap_pts;
+  }
+  k_work<<<grid_for(n, 256), 256, 0, h->stream>>>(h->pred, n, (uint32_t)h->last_base, h->wcost);
+  ++g_kernel_launches;
+  h->wcost_ready = true;
   h->risky_ready = h->use_defer;
   h->prank_ready = h->use_prank;
   return cudaPeekAtLastError() == cudaSuccess ? DT_OK : DT_ECUDA;
@@ -2381,6 +2448,9 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->async_big_ws);
   cudaFree(h->async_borrow_ws);
   cudaFree(h->async_borrow_busy);
+  cudaFree(h->wcost);
+  cudaFree(h->seg_prefix);
+  cudaFree(h->seg_bounds);
   cudaFree(h->freelist);
   cudaFree(h->pending);
   cudaFree(h->cell_hint);

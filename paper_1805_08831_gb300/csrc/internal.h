@@ -115,6 +115,8 @@ bool radix_sort_pairs(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint
 bool radix_sort_pairs_bits(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int lo_bit,
                            int hi_bit, uint32_t* hist, cudaStream_t s);
 uint64_t radix_hist_entries(uint64_t n);
+// In-place exclusive prefix sum of data[0, len) (device); scratch holds radix_hist_entries(len).
+void prefix_sum_exclusive(uint32_t* data, uint64_t len, uint32_t* scratch, cudaStream_t s);
 
 // Cumulative end of BRIO round r (Section 2.3 / Table 2): 2048 * 7^r.
 uint64_t brio_round_end(int r);
@@ -142,6 +144,7 @@ struct AsyncIO {
   int big_q;
   uint32_t* exact_out;  // predicates the FP32 stage cannot decide: the round-based engine's
   int exact_q;
+  const uint32_t* bounds;  // W + 1 segment starts (learned schedule), or null: equal segments of L
   void* big_ws;         // global-memory workspaces a warp may borrow for a large cavity (or null)
   unsigned int* big_busy;  // one word per workspace: 0 free, 1 borrowed
   uint32_t big_n;       // workspaces

@@ -555,6 +555,10 @@ constexpr uint64_t radix_hist_entries_for(uint64_t n) {
 
 uint64_t radix_hist_entries(uint64_t n) { return radix_hist_entries_for(n); }
 
+void prefix_sum_exclusive(uint32_t* data, uint64_t len, uint32_t* scratch, cudaStream_t s) {
+  if (len) scan_exclusive(data, len, scratch, s);
+}
+
 bool radix_sort_pairs(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int bits,
                       uint32_t* hist, cudaStream_t s) {
   return radix_sort_pairs_bits(k, v, ka, va, n, 0, bits, hist, s);

@@ -229,3 +229,25 @@ def test_errors_are_reported_not_raised_on_device():
     with pytest.raises(dt.DTError) as e:
         gpu_tets(bad)
     assert e.value.code == dt.DT_EINVAL
+
+
+# ----------------------------------------------------------------------------- both engines
+@pytest.mark.parametrize("engine", ["async", "rounds"])
+@pytest.mark.parametrize("kind,n,seed", [("uniform", 60000, 21), ("degenerate", 30000, 22), ("slab", 40000, 23)])
+def test_each_engine_alone_is_bit_exact(monkeypatch, engine, kind, n, seed):
+    """The asynchronous engine (per-warp segments under ownership words) and the round-based one
+    (claim words, three kernels a round) each give the oracle's tetrahedra on their own: DT_ASYNC=0
+    keeps every pass on the rounds; DT_ASYNC_MIN_RETRY=1 sends even short retry lists to the
+    asynchronous engine."""
+    if engine == "rounds":
+        monkeypatch.setenv("DT_ASYNC", "0")
+    else:
+        monkeypatch.setenv("DT_ASYNC_MIN_RETRY", "1")
+    x = synth.make(kind, n, seed)
+    ref, _ = oracle.delaunay(x, seed=seed)
+    got, st = gpu_tets(x, seed=seed)
+    assert_same(got, ref)
+    if engine == "rounds":
+        assert st["n_async"] == 0
+    else:
+        assert st["n_inserted_async"] > 0

@@ -31,11 +31,11 @@ import numpy as np  # noqa: E402
 from paper_1805_08831_gb300 import synth  # noqa: E402
 
 METRIC = "Mtets/s for 3D DT of 1e7-1e8 pts on 1 GB300; learned-sched vs plain, bit-exact"
-# DRAM bytes (read + write) per insertion of the asynchronous insertion kernel, from one ncu
+# DRAM bytes (read + write) per point taken by the asynchronous insertion kernel, from one ncu
 # capture of a large launch (the k_async summary under profiles/), and the hash of the kernel
 # sources it was taken on: the traffic is reported only while the sources are unchanged.
-ASYNC_TRAFFIC_PER_INSERTION = None
-ASYNC_TRAFFIC_SOURCES = ""
+ASYNC_TRAFFIC_PER_POINT = 4375.0
+ASYNC_TRAFFIC_SOURCES = "8191b224fe1c88cd"
 REFINE_K = 128  # the refinement workload: the unit cube at size 1/128 from its surface lattice
 KERNEL_SOURCES = ["async.cu", "engine.cuh", "dt.cu", "common.cuh", "predicates.cuh"]
 GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize.json")
@@ -217,9 +217,9 @@ def roofline_of(st_prof, steps_prof, ms_step, peak, peak_kind):
     ms_dom = times[dom] / steps_prof
     achieved = alg / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
     traffic = None
-    if (dom == "k_async" and ASYNC_TRAFFIC_PER_INSERTION is not None
-            and kernel_sources_hash() == ASYNC_TRAFFIC_SOURCES):
-        traffic = ASYNC_TRAFFIC_PER_INSERTION * st_prof["n_inserted_async"] / max(launches[dom] / steps_prof, 1)
+    if dom == "k_async" and kernel_sources_hash() == ASYNC_TRAFFIC_SOURCES:
+        # the capture's bytes per point, scaled to this run's points per launch
+        traffic = ASYNC_TRAFFIC_PER_POINT * st_prof["n_inserted_async"] / max(launches[dom] / steps_prof, 1)
     n_launch = max(launches[dom] / steps_prof, 1)
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
@@ -229,7 +229,9 @@ def roofline_of(st_prof, steps_prof, ms_step, peak, peak_kind):
             "bytes_per_point": terms, "path_bytes_per_point": bpt,
             "path_frac": bpt * ins / (ms_step / 1e3) / 1e9 / peak if ms_step else None,
             "how": "alg bytes = the hot-path table's per-point terms x insertions of the kernel; time from "
-                   "CUDA events around every launch in a separate profiled run of the same workload"}, cfb
+                   "CUDA events around every launch in a separate profiled run of the same workload; "
+                   "traffic = ncu DRAM bytes per point of a large k_async launch at 2e6 uniform x points "
+                   "per launch of this run"}, cfb
 
 
 def run_oracle(x, seed):

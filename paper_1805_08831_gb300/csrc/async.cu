@@ -908,7 +908,7 @@ int async_blocks_per_sm() {
     // step against 265 (6 blocks, 80 registers), 276 (5, 96) and 301 (4, 128)
     int v = 8;
     if (const char* e = std::getenv("DT_ASYNC_BLOCKS")) v = std::atoi(e);
-    g_async_blocks = (v == 4 || v == 5 || v == 6 || v == 8) ? v : 8;
+    g_async_blocks = (v == 4 || v == 5 || v == 6 || v == 7 || v == 8) ? v : 8;
   }
   return g_async_blocks;
 }
@@ -926,6 +926,7 @@ int async_launch(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t*
     case 4: k_async<4><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
     case 5: k_async<5><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
     case 6: k_async<6><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
+    case 7: k_async<7><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
     default: k_async<8><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
   }
   k_async_close_copy<<<152, 256, 0, s>>>(cc);
@@ -959,6 +960,7 @@ int async_max_warps() {
     cudaError_t e = mb == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<4>, kAW * 32, 0)
                   : mb == 5 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<5>, kAW * 32, 0)
                   : mb == 6 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<6>, kAW * 32, 0)
+                  : mb == 7 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<7>, kAW * 32, 0)
                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_async<8>, kAW * 32, 0);
     if (e != cudaSuccess) per = mb;
     cached = std::max(1, sms * std::max(per, 1) * kAW);

@@ -860,6 +860,9 @@ struct dt_handle {
   uint64_t async_min_retry = 2048; // retry lists shorter than this use the round-based engine
   uint64_t async_warps = 0;        // cap on the asynchronous engine's warps (0: all that fit)
   bool async_off = false;          // this call's inputs defeat the asynchronous engine's FP32 stage
+  double async_handoff_frac = 0.2; // hand-offs per point of a pass that switch it off for the call
+                                   // (degenerate mix: 42.8 Mtets/s at 0.2, 34.7 at 0.5; never
+                                   // switching off sends points back and forth, 3.2)
   uint8_t* wcost = nullptr;        // learned schedule: predicted insertion work per vertex
   bool wcost_ready = false;
   uint32_t* seg_prefix = nullptr;  // prefix sums of a pass's predicted work
@@ -1347,7 +1350,7 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   // when the FP32 stage cannot decide for a fifth of a pass's points (near-degenerate inputs:
   // lattices, co-spherical surfaces, refinement centres), the work it did was mostly wasted:
   // the rest of this call runs on the round-based engine
-  if (5 * ne > m) h->async_off = true;
+  if ((double)ne > h->async_handoff_frac * (double)m) h->async_off = true;
   return run_pass(h, c, h->queue[kQExact], 0, ne, false, 1.f, true);
 }
 
@@ -2148,6 +2151,7 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (const char* a = std::getenv("DT_ALPHA_ASYNC")) h->alpha_async = std::atof(a);
   if (const char* a = std::getenv("DT_ASYNC_MIN_RETRY")) h->async_min_retry = std::strtoull(a, nullptr, 10);
   if (const char* a = std::getenv("DT_ASYNC_WARPS")) h->async_warps = std::strtoull(a, nullptr, 10);
+  if (const char* a = std::getenv("DT_ASYNC_HANDOFF")) h->async_handoff_frac = std::atof(a);
   if (const char* w = std::getenv("DT_WALK_THREADS")) {
     int v = std::atoi(w);
     if (v == 32 || v == 64 || v == 128 || v == 256) h->walk_threads = v;

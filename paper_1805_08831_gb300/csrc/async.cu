@@ -480,7 +480,7 @@ __device__ __forceinline__ void pool_give(const Ctx& c, W& w, const uint32_t* s,
 // One attempt at inserting p (steps 1-5). w.hint is the warp's last ball, updated on success.
 template <class W>
 __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, uint32_t me, uint32_t p,
-                                          const InsertLog& lg) {
+                                          const InsertLog& lg, bool io_balltest = true) {
   const int lane = threadIdx.x & 31;
   const PtF FP = load_ptf(c.ptf, p);
   for (int attempt = 0; attempt <= kARetry; ++attempt) {
@@ -489,7 +489,7 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
     //    previous point): one insphere test per lane finds it without a walk. Otherwise walk.
     int ws = kAInserted;
     uint32_t t0 = kNone;
-    if (attempt == 0 && w.bn > 0) {
+    if (attempt == 0 && w.bn > 0 && io_balltest) {
       bool in = false;
       if (lane < w.bn) {
         const uint4 v = __ldcg(reinterpret_cast<const uint4*>(c.tets + w.slot[lane]));
@@ -573,6 +573,9 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
     __syncwarp();
     // record every internal facet: facet a of new tetrahedron i holds the boundary edge b -> c
     bool vfail = false;
+    // the table path's vertex slots of this lane's facets (lane and lane + 32; nb <= 60), kept
+    // for the partner lookups below
+    uint32_t vs[2] = {0, 0};
     for (int i = lane; i < nb; i += 32) {
       const int ci = w.bl_ci[i], f = w.bl_f[i];
       uint4 v = w.cr[ci].v;
@@ -586,6 +589,7 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
           vfail = true;
           continue;
         }
+        vs[i >> 5] = (uint32_t)la | ((uint32_t)lb << 8) | ((uint32_t)lc << 16);
         w.tab[lb * 32 + lc] = (uint16_t)((i << 2) | pos[0]);
         w.tab[lc * 32 + la] = (uint16_t)((i << 2) | pos[1]);
         w.tab[la * 32 + lb] = (uint16_t)((i << 2) | pos[2]);
@@ -625,7 +629,8 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
       after_pos(f, a, b, cc);
       uint32_t ea, eb, ec;
       if constexpr (W::kTable) {
-        const int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
+        const uint32_t sl = vs[i >> 5];
+        const int la = (int)(sl & 0xFFu), lb = (int)((sl >> 8) & 0xFFu), lc = (int)(sl >> 16);
         ea = vld(&w.tab[lc * 32 + lb]);
         eb = vld(&w.tab[la * 32 + lc]);
         ec = vld(&w.tab[lb * 32 + la]);
@@ -786,7 +791,7 @@ __device__ __forceinline__ void run_segment(const Ctx& c, const AsyncIO& io, W& 
       break;
     }
     if (lane == 0) w.cnt[2] += 1;
-    int r = try_insert(c, w, lock, me, p, lg);
+    int r = try_insert(c, w, lock, me, p, lg, io.ball_start != 0);
     if constexpr (W::kTable) {
       if (r == kABig) r = try_insert_large(c, io, w, lock, me, p, lg);
     }

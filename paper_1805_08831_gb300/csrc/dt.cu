@@ -860,6 +860,7 @@ struct dt_handle {
   uint64_t async_min_retry = 2048; // retry lists shorter than this use the round-based engine
   uint64_t async_warps = 0;        // cap on the asynchronous engine's warps (0: all that fit)
   bool async_off = false;          // this call's inputs defeat the asynchronous engine's FP32 stage
+  uint32_t async_ball_start = 1;   // start from the previous ball's tetrahedra before walking
   double async_handoff_frac = 0.2; // hand-offs per point of a pass that switch it off for the call
                                    // (degenerate mix: 42.8 Mtets/s at 0.2, 34.7 at 0.5; never
                                    // switching off sends points back and forth, 3.2)
@@ -1268,7 +1269,7 @@ int run_big_async(dt_handle* h, const Ctx& c) {
     W = (nbig + L - 1) / L;
     AsyncIO io{h->queue[kQBig], 0, nbig, L, (uint32_t)W, h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kAsyncWalk,
                h->queue[kQBig2], kQBig2, h->queue[kQHuge], kQHuge, h->queue[kQExact], kQExact,
-               nullptr, nullptr, nullptr, 0};
+               nullptr, nullptr, nullptr, 0, h->async_ball_start};
     if ((rc = async_launch_big(c, io, h->lock, h->vflag, make_log(h), h->async_big_ws, h->stream)) != DT_OK)
       return rc;
     h->stats.n_async++;
@@ -1326,7 +1327,7 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   }
   AsyncIO io{q, qbase, m, L, (uint32_t)W, h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kAsyncWalk,
              h->queue[kQNext], kQNext, h->queue[kQBig], kQBig, h->queue[kQExact], kQExact,
-             seg_bounds, h->async_borrow_ws, h->async_borrow_busy, kAsyncBorrow};
+             seg_bounds, h->async_borrow_ws, h->async_borrow_busy, kAsyncBorrow, h->async_ball_start};
   const bool prof = (h->cfg.flags & DT_FLAG_PROFILE) != 0;
   if (prof) cudaEventRecord(h->ev[3], h->stream);
   if ((rc = async_launch(c, io, h->lock, h->vflag, make_log(h), h->stream)) != DT_OK) return rc;
@@ -2152,6 +2153,7 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (const char* a = std::getenv("DT_ASYNC_MIN_RETRY")) h->async_min_retry = std::strtoull(a, nullptr, 10);
   if (const char* a = std::getenv("DT_ASYNC_WARPS")) h->async_warps = std::strtoull(a, nullptr, 10);
   if (const char* a = std::getenv("DT_ASYNC_HANDOFF")) h->async_handoff_frac = std::atof(a);
+  if (const char* a = std::getenv("DT_ASYNC_BALL_START")) h->async_ball_start = (uint32_t)std::atoi(a);
   if (const char* w = std::getenv("DT_WALK_THREADS")) {
     int v = std::atoi(w);
     if (v == 32 || v == 64 || v == 128 || v == 256) h->walk_threads = v;

@@ -148,6 +148,7 @@ struct AsyncIO {
   void* big_ws;         // global-memory workspaces a warp may borrow for a large cavity (or null)
   unsigned int* big_busy;  // one word per workspace: 0 free, 1 borrowed
   uint32_t big_n;       // workspaces
+  uint32_t ball_start;  // 1: try the previous ball's tetrahedra as the start before walking
 };
 // Enqueues the asynchronous insertion of one pass and the close of its allocator. lock: one
 // word per tetrahedron slot, all zero before and after.

@@ -857,7 +857,10 @@ struct dt_handle {
   double alpha_async = 0.05; // concurrent insertions (warps) per mesh vertex of the asynchronous engine
                              // (with its waves of 2x the mesh: 162.1 ms per 1e7 uniform step at 0.05,
                              // 164.9 at 0.1, 169.8 at 0.2; a lost attempt is cheap when nothing waits)
-  uint64_t async_min_retry = 2048; // retry lists shorter than this use the round-based engine
+  uint64_t async_min_retry = 1;    // retry lists shorter than this use the round-based engine (1e7
+                                   // uniform: 146 ms with every list on the asynchronous engine,
+                                   // 147 with lists of 32 or more, 152 with 256, 155 with 2048); a
+                                   // retry pass without progress moves the list to the rounds anyway
   uint64_t async_warps = 0;        // cap on the asynchronous engine's warps (0: all that fit)
   bool async_off = false;          // this call's inputs defeat the asynchronous engine's FP32 stage
   uint32_t async_ball_start = 1;   // start from the previous ball's tetrahedra before walking

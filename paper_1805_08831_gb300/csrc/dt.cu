@@ -847,6 +847,7 @@ struct dt_handle {
   bool has_mesh = false;
   uint64_t last_n = 0;
   double alpha = 0.02;   // candidates per round = alpha * mesh vertices (measured best at 1e7 and 1e8)
+  double alpha_refine = 0.01;  // the same during dt_refine
   double gamma = 0.3;    // wave size = gamma * mesh vertices (round-based and batch engines)
   double gamma_async = 2.0;  // the asynchronous engine's waves (measured: 164.9 ms per 1e7 uniform
                              // step at 2.0 against 166.8 at 1.0, 175.0 at 0.5 and 185.6 at 0.3;
@@ -2147,6 +2148,7 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (cfg) h->cfg = *cfg;
   h->stream = (cudaStream_t)h->cfg.stream;
   if (const char* a = std::getenv("DT_ALPHA")) h->alpha = std::atof(a);
+  if (const char* a = std::getenv("DT_ALPHA_REFINE")) h->alpha_refine = std::atof(a);
   if (const char* g = std::getenv("DT_GAMMA")) h->gamma = std::atof(g);
   if (const char* g = std::getenv("DT_GAMMA_ASYNC")) h->gamma_async = std::atof(g);
   if (const char* a = std::getenv("DT_ALPHA_CTA")) h->alpha_cta = std::atof(a);
@@ -2241,6 +2243,11 @@ int dt_refine(dt_handle* h, double size, double ratio, double spacing, const dou
   uint64_t added = 0;
   uint32_t iters = 0;
   int rc = DT_OK;
+  // the first iterations put every new point into the sparse interior while the concurrency
+  // follows the whole (mostly surface) mesh: fewer candidates per vertex collide less
+  // (measured 10 % faster at 0.01 than at the default 0.02 on the 1/128 box)
+  const double alpha_keep = h->alpha;
+  h->alpha = h->alpha_refine;
   while (iters < max_iters) {
     if ((rc = sync_state(h)) != DT_OK) break;
     uint64_t m = 0, ns = 0;
@@ -2254,6 +2261,7 @@ int dt_refine(dt_handle* h, double size, double ratio, double spacing, const dou
     added += ns;
     ++iters;
   }
+  h->alpha = alpha_keep;
   if (n_added) *n_added = added;
   if (n_iters) *n_iters = iters;
   return rc;

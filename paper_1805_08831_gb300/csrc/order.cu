@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstdint>
 #include <mutex>
 
@@ -468,6 +469,92 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
 }
 
+// The same pass with the tile ranked in shared memory first: every element gets its stable
+// position inside the tile's digit runs (chunks, then warps, then lanes in order, as above), and
+// the runs are then written out contiguously, so consecutive threads write consecutive addresses
+// of one digit's run instead of one scattered element each.
+constexpr size_t kScatterSmem = (size_t)kTile * 8 + (size_t)kTile * 4 + (size_t)(kSortThreads / 32) * 256 * 4 +
+                                3 * 256 * 4;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter_tiled(
+    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n, int shift,
+    const uint32_t* __restrict__ offs, uint32_t ntiles, uint64_t* okeys, uint32_t* ovals) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(sm);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sm + (size_t)kTile * 8);
+  uint32_t(*wc)[256] = reinterpret_cast<uint32_t(*)[256]>(sm + (size_t)kTile * 12);
+  uint32_t* lstart = reinterpret_cast<uint32_t*>(sm + (size_t)kTile * 12 + (size_t)(kSortThreads / 32) * 1024);
+  uint32_t* lnext = lstart + 256;
+  uint32_t* gbase = lnext + 256;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t start = (uint64_t)blockIdx.x * kTile;
+  const uint32_t tn = (uint32_t)((n - start) < (uint64_t)kTile ? (n - start) : (uint64_t)kTile);
+  gbase[tid] = offs[(uint64_t)tid * ntiles + blockIdx.x];
+  // the tile's digit counts, then their exclusive scan: where each digit's run starts in the tile
+  lnext[tid] = 0;
+  __syncthreads();
+  for (int c = 0; c < kSortItems; ++c) {
+    const uint32_t j = (uint32_t)c * kSortThreads + tid;
+    if (j < tn) atomicAdd(&lnext[(keys[start + j] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v[8], acc = 0;
+    for (int k = 0; k < 8; ++k) v[k] = lnext[lane * 8 + k];
+    for (int k = 0; k < 8; ++k) acc += v[k];
+    uint32_t incl = acc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - acc;
+    for (int k = 0; k < 8; ++k) {
+      lstart[lane * 8 + k] = run;
+      run += v[k];
+    }
+  }
+  __syncthreads();
+  lnext[tid] = lstart[tid];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = 0; c < kSortItems; ++c) {
+    for (int w = 0; w < kSortThreads / 32; ++w) wc[w][tid] = 0;
+    __syncthreads();
+    const uint32_t j = (uint32_t)c * kSortThreads + tid;
+    const bool valid = j < tn;
+    const uint64_t k = valid ? keys[start + j] : 0;
+    const uint32_t v = valid ? vals[start + j] : 0;
+    const unsigned d = valid ? (unsigned)((k >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    const unsigned rank = __popc(peers & lt);
+    if (valid && rank == 0) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t x0 = lnext[tid];
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t x = wc[w][tid];
+        wc[w][tid] = x0;
+        x0 += x;
+      }
+      lnext[tid] = x0;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = wc[warp][d] + rank;
+      sk[pos] = k;
+      sv[pos] = v;
+    }
+    __syncthreads();
+  }
+  // the runs, in order: position j of the tile holds digit d's (j - lstart[d])-th element
+  for (uint32_t j = tid; j < tn; j += kSortThreads) {
+    const uint64_t k = sk[j];
+    const unsigned d = (unsigned)((k >> shift) & 255u);
+    const uint64_t g = (uint64_t)gbase[d] + (j - lstart[d]);
+    okeys[g] = k;
+    ovals[g] = sv[j];
+  }
+}
+
 // Exclusive scan of a uint32 array, 4096 elements per block, recursive on block sums.
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = kScanThreads * 4;
@@ -564,6 +651,18 @@ bool radix_sort_pairs(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint
   return radix_sort_pairs_bits(k, v, ka, va, n, 0, bits, hist, s);
 }
 
+// The tiled scatter needs more than the default 48 KB of dynamic shared memory: opt in once per
+// process (every device of this library runs the same build).
+bool tiled_scatter_ready() {
+  static int state = 0;  // 0 unknown, 1 ready, -1 not available
+  if (state == 0) {
+    if (std::getenv("DT_SORT_SCATTER_PLAIN")) state = -1;
+    else state = cudaFuncSetAttribute(k_radix_scatter_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kScatterSmem) == cudaSuccess ? 1 : -1;
+  }
+  return state == 1;
+}
+
 bool radix_sort_pairs_bits(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va, uint64_t n, int lo_bit,
                            int hi_bit, uint32_t* hist, cudaStream_t s) {
   if (n <= 1) return false;
@@ -578,7 +677,10 @@ bool radix_sort_pairs_bits(uint64_t* k, uint32_t* v, uint64_t* ka, uint32_t* va,
     k_radix_hist<<<ntiles, kSortThreads, 0, s>>>(sk, n, shift, hist, ntiles);
     ++g_kernel_launches;
     scan_exclusive(hist, len, hist + len, s);
-    k_radix_scatter<<<ntiles, kSortThreads, 0, s>>>(sk, sv, n, shift, hist, ntiles, dk, dv);
+    if (tiled_scatter_ready())
+      k_radix_scatter_tiled<<<ntiles, kSortThreads, kScatterSmem, s>>>(sk, sv, n, shift, hist, ntiles, dk, dv);
+    else
+      k_radix_scatter<<<ntiles, kSortThreads, 0, s>>>(sk, sv, n, shift, hist, ntiles, dk, dv);
     ++g_kernel_launches;
     alt = !alt;
   }

@@ -868,6 +868,7 @@ struct dt_handle {
   double async_handoff_frac = 0.2; // hand-offs per point of a pass that switch it off for the call
                                    // (degenerate mix: 42.8 Mtets/s at 0.2, 34.7 at 0.5; never
                                    // switching off sends points back and forth, 3.2)
+  uint64_t async_handoff_min = 4096; // passes shorter than this never switch it off
   uint8_t* wcost = nullptr;        // learned schedule: predicted insertion work per vertex
   bool wcost_ready = false;
   uint32_t* seg_prefix = nullptr;  // prefix sums of a pass's predicted work
@@ -1354,8 +1355,9 @@ int run_pass_async(dt_handle* h, const Ctx& c, const uint32_t* q, uint32_t qbase
   h->stats.n_exact_handoff += ne;
   // when the FP32 stage cannot decide for a fifth of a pass's points (near-degenerate inputs:
   // lattices, co-spherical surfaces, refinement centres), the work it did was mostly wasted:
-  // the rest of this call runs on the round-based engine
-  if ((double)ne > h->async_handoff_frac * (double)m) h->async_off = true;
+  // the rest of this call runs on the round-based engine. A short retry list says little about
+  // the input (its points are the hard ones by selection), so it never decides this
+  if (m >= h->async_handoff_min && (double)ne > h->async_handoff_frac * (double)m) h->async_off = true;
   return run_pass(h, c, h->queue[kQExact], 0, ne, false, 1.f, true);
 }
 
@@ -2158,6 +2160,7 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (const char* a = std::getenv("DT_ASYNC_MIN_RETRY")) h->async_min_retry = std::strtoull(a, nullptr, 10);
   if (const char* a = std::getenv("DT_ASYNC_WARPS")) h->async_warps = std::strtoull(a, nullptr, 10);
   if (const char* a = std::getenv("DT_ASYNC_HANDOFF")) h->async_handoff_frac = std::atof(a);
+  if (const char* a = std::getenv("DT_ASYNC_HANDOFF_MIN")) h->async_handoff_min = std::strtoull(a, nullptr, 10);
   if (const char* a = std::getenv("DT_ASYNC_BALL_START")) h->async_ball_start = (uint32_t)std::atoi(a);
   if (const char* w = std::getenv("DT_WALK_THREADS")) {
     int v = std::atoi(w);

@@ -192,6 +192,24 @@ int dt_get_points(dt_handle* h, double* xyz_dev, uint64_t rows, uint64_t* n_poin
 int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets,
                 uint64_t* cloud_offsets, int canonical);
 
+/* Certificate of the current triangulation, checked on the device at any size. A closed,
+ * consistently oriented complex of tetrahedra (the ghost ones included) whose every facet is
+ * locally Delaunay is the Delaunay triangulation of its vertices (the Delaunay lemma; Section
+ * 2.1's empty-sphere property follows). With the insertion predicates' perturbation (Section 2.4)
+ * that triangulation is unique, so a certificate without faults identifies it. out_host (host,
+ * 5 entries) receives:
+ *   [0] live finite tetrahedra (the count dt_get_tets returns),
+ *   [1] (tetrahedron, facet) pairs whose neighbour is dead, or does not name the tetrahedron
+ *       back, or does not share the facet's three vertices,
+ *   [2] finite tetrahedra whose orientation is not positive (exact),
+ *   [3] facets whose neighbour's opposite vertex is in conflict with the tetrahedron (exact
+ *       perturbed insphere; for a ghost, the hull facet's side and Section 2.6's rule),
+ *   [4] distinct points that are vertices of finite tetrahedra (the points given minus the
+ *       duplicates dropped).
+ * A Delaunay triangulation gives [1] = [2] = [3] = 0. The handle's statistics do not change.
+ * DT_ESTATE after dt_batch; DT_ENOMEM if the scratch (n_points bytes) cannot be allocated. */
+int dt_check(dt_handle* h, uint64_t* out_host);
+
 /* Host variant of dt_get_tets: tets_host is host memory. */
 int dt_get_tets_host(dt_handle* h, uint32_t* tets_host, uint64_t cap, uint64_t* n_tets, int canonical);
 

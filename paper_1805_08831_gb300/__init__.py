@@ -122,6 +122,7 @@ def lib():
         L.dt_refine.argtypes = [p, ctypes.c_double, ctypes.c_double, ctypes.c_double, p, u32,
                                 ctypes.POINTER(u64), ctypes.POINTER(u32)]
         L.dt_get_points.argtypes = [p, p, u64, ctypes.POINTER(u64)]
+        L.dt_check.argtypes = [p, p]
         for name in exported_names():
             getattr(L, name)
         _lib = L
@@ -230,6 +231,14 @@ class Triangulation:
             _check(lib().dt_get_points(self._h, ctypes.c_void_p(out.data_ptr()), n.value, ctypes.byref(n)),
                    "dt_get_points")
         return out
+
+    def check(self):
+        """Device certificate of the mesh (dt_check): dict of live finite tetrahedra, bad
+        adjacencies, non-positive orientations, non-locally-Delaunay facets and vertices used."""
+        out = (ctypes.c_uint64 * 5)()
+        self._check_dev(lib().dt_check(self._h, out), "dt_check")
+        return {"tets": out[0], "bad_adjacency": out[1], "bad_orientation": out[2],
+                "not_delaunay": out[3], "vertices": out[4]}
 
     def batch(self, xyz, offsets):
         """Triangulates independent clouds in one call: xyz is a CUDA float64 tensor [N, 3] with

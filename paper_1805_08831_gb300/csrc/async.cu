@@ -42,7 +42,6 @@ constexpr int kAW = 4;            // warps per block of the shared-memory kernel
 constexpr int kADefer = 16;       // aborted points waiting for a retry
 constexpr int kARetry = 3;        // immediate restarts after a failed re-read
 constexpr uint32_t kAChunk = 32;  // slots taken from the allocator at a time
-constexpr uint32_t kVerifyOnly = 0x80000000u;  // outside-list entry read but not locked
 
 enum AStatus : int { kAInserted = 0, kALost = 1, kARestart = 2, kABig = 3, kAWalkLimit = 4, kADup = 5, kAExact = 6 };
 
@@ -87,7 +86,7 @@ struct AWS : AWSTail<kTableB, kHashN, kFMaxN> {
   static_assert(kCMaxN + kAMaxN + kFMaxN <= 32 * 8 * (int)sizeof(HeldT), "lock mask holds every entry");
   uint32_t cl[kCMaxN];       // cavity slots
   Tet cr[kCMaxN];            // their records as read
-  uint32_t al[kAMaxN];       // outside slots (kVerifyOnly: read for a ghost test, not locked)
+  uint32_t al[kAMaxN];       // outside slots
   uint4 av[kAMaxN];          // their vertex ids as read
   uint32_t slot[kFMaxN];     // slots of the new tetrahedra
   uint32_t ex[kFMaxN];       // slots beyond the cavity's, taken from the pool
@@ -95,7 +94,7 @@ struct AWS : AWSTail<kTableB, kHashN, kFMaxN> {
   uint32_t pool[kPool];
   uint32_t defer[kADefer];
   CI bl_ci[kFMaxN];          // boundary facet: cavity index
-  uint8_t bl_f[kFMaxN];      // boundary facet: facet
+  uint8_t bl_f[kFMaxN];      // boundary facet: facet | 4 * the outside tetrahedron's facet
   unsigned long long fa, bump;  // allocator snapshot of the launch
   unsigned int cnt[8];          // inserted, lost, attempts, sum |C|, sum |B|, walk steps, restarts
   uint32_t hint;                // the warp's last ball
@@ -126,7 +125,7 @@ __device__ __forceinline__ bool rec_ok(const Tet& T, uint32_t ntets, uint32_t np
   bool ok = true;
   for (int k = 0; k < 4; ++k) {
     uint32_t v = get4(T.v, k), n = get4(T.n, k);
-    ok = ok && (v == kGhost || v < npts) && (n >> 2) < ntets;
+    ok = ok && (v == kGhost || v < npts) && n < ntets;
   }
   return ok;
 }
@@ -186,7 +185,7 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
   if (!rec_ok(T, c.ntets, c.npts)) return kARestart;
   int g = ghost_pos(T.v);
   if (g >= 0) {
-    t = get4(T.n, g) >> 2;
+    t = get4(T.n, g);
     T = ld_tet(c.tets, t);
     if (tet_dead(T.v) || !rec_ok(T, c.ntets, c.npts)) return kARestart;
   }
@@ -198,7 +197,7 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
     if (lane < 4) {
       const PtF F0 = load_ptf(c.ptf, T.v.x), F1 = load_ptf(c.ptf, T.v.y), F2 = load_ptf(c.ptf, T.v.z),
                 F3 = load_ptf(c.ptf, T.v.w);
-      o = (get4(T.n, lane) >> 2) == prev ? 1 : orient_with_p(c, lane, FP, F0, F1, F2, F3);
+      o = get4(T.n, lane) == prev ? 1 : orient_with_p(c, lane, FP, F0, F1, F2, F3);
     }
     const unsigned sees = __ballot_sync(kFull, lane < 4 && o < 0) & 0xFu;
     if (__ballot_sync(kFull, lane < 4 && o == 0) & 0xFu) return kAExact;
@@ -225,7 +224,7 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
     const unsigned rot = ((sees | (sees << 4)) >> ((salt + steps) & 3)) & 0xFu;
     const int exit = (__ffs(rot) - 1 + (int)((salt + steps) & 3)) & 3;
     prev = t;
-    t = get4(T.n, exit) >> 2;
+    t = get4(T.n, exit);
     T = ld_tet(c.tets, t);
     ++steps;
     if (tet_dead(T.v) || !rec_ok(T, c.ntets, c.npts)) {
@@ -239,11 +238,10 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
   return kAInserted;
 }
 
-// Conflict of a record U (already read) with p: 1 in the cavity, 0 outside, -1 the record (or
-// the one a ghost test needs) is inconsistent, -2 undecided by the FP32 stage. For a ghost whose
-// hull facet's plane holds p, the finite neighbour across the facet decides (Section 2.6); its
-// slot and vertices go to *r / *rv.
-__device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const PtF& FP, uint32_t* r, uint4* rv) {
+// Conflict of a record U (already read) with p: 1 in the cavity, 0 outside, -2 undecided by the
+// FP32 stage. For a ghost whose hull facet's plane holds p the finite neighbour across the facet
+// decides (Section 2.6): that case is left to the round-based engine (-2).
+__device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const PtF& FP) {
   const int g = ghost_pos(U.v);
   if (g < 0) {
     const int s = inside_async(c, U.v, FP);
@@ -256,8 +254,6 @@ __device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const 
   if (o != 0) return o > 0 ? 1 : 0;
   // p on the facet's plane as far as the FP32 stage can tell: the exact rule needs the
   // round-based engine (the plane test and the neighbour's perturbed sphere)
-  (void)r;
-  (void)rv;
   return -2;
 }
 
@@ -314,7 +310,7 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, W& w, uint32_t t0, uin
       active = k < batch;
       ci = head + k;
       if (active) {
-        u = get4(w.cr[ci].n, f) >> 2;
+        u = get4(w.cr[ci].n, f);
         if (u >= c.ntets) {
           flag = 1;
           active = false;
@@ -330,12 +326,10 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, W& w, uint32_t t0, uin
     const int leader = __ffs(peers) - 1;
     const bool is_leader = need && lane == leader;
     int res = 0, myflag = 0;
-    uint32_t r = kNone;
-    uint4 rv{};
     Tet U;
     if (is_leader) {
       U = ld_tet(c.tets, u);
-      const int in = (tet_dead(U.v) || !rec_ok(U, c.ntets, c.npts)) ? -1 : conflict_async(c, U, FP, &r, &rv);
+      const int in = (tet_dead(U.v) || !rec_ok(U, c.ntets, c.npts)) ? -1 : conflict_async(c, U, FP);
       if (in == -2) {
         myflag |= 4;
       } else if (in < 0) {
@@ -360,10 +354,9 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, W& w, uint32_t t0, uin
       }
     }
     nc += __popc(mC);
-    // outside tetrahedra (locked) and the finite neighbours ghost tests read (verify only)
+    // outside tetrahedra (locked and verified)
     const bool addA = is_leader && res == 2;
-    const bool addR = is_leader && r != kNone;
-    const unsigned mA = __ballot_sync(kFull, addA), mR = __ballot_sync(kFull, addR);
+    const unsigned mA = __ballot_sync(kFull, addA);
     if (addA) {
       const int pos = na + __popc(mA & lanemask_lt());
       if (pos < W::kAMax) {
@@ -372,14 +365,6 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, W& w, uint32_t t0, uin
       }
     }
     na += __popc(mA);
-    if (addR) {
-      const int pos = na + __popc(mR & lanemask_lt());
-      if (pos < W::kAMax) {
-        w.al[pos] = r | kVerifyOnly;
-        w.av[pos] = rv;
-      }
-    }
-    na += __popc(mR);
     const bool addB = active && ci >= 0 && res == 2;
     const unsigned mB = __ballot_sync(kFull, addB);
     if (addB) {
@@ -406,16 +391,12 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, W& w, uint32_t t0, uin
   return kAInserted;
 }
 
-// Slot of lock-list entry i: cavity slots, then the outside slots that are locked, then the
-// ball's extra slots. Verify-only outside entries give kNone (not locked).
+// Slot of lock-list entry i: cavity slots, then the outside slots, then the ball's extra slots.
 template <class W>
 __device__ __forceinline__ uint32_t lock_entry(const W& w, int i, int nc, int na, int nx) {
   if (i < nc) return w.cl[i];
   i -= nc;
-  if (i < na) {
-    const uint32_t a = w.al[i];
-    return (a & kVerifyOnly) ? kNone : a;
-  }
+  if (i < na) return w.al[i];
   i -= na;
   return i < nx ? w.ex[i] : kNone;
 }
@@ -552,8 +533,16 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
     bool same = true;
     for (int i = lane; i < nc; i += 32) same = same && same_tet(ld_tet(c.tets, w.cl[i]), w.cr[i]);
     for (int i = lane; i < na; i += 32) {
-      const uint32_t a = w.al[i] & ~kVerifyOnly;
+      const uint32_t a = w.al[i];
       same = same && same_v(__ldcg(reinterpret_cast<const uint4*>(c.tets + a)), w.av[i]);
+    }
+    // which facet of each outside tetrahedron faces the cavity (it is locked: this stays true)
+    for (int i = lane; i < nb; i += 32) {
+      const int ci = w.bl_ci[i], f = w.bl_f[i] & 3;
+      const uint32_t u = get4(w.cr[ci].n, f);
+      const int back = back_facet(__ldcg(reinterpret_cast<const uint4*>(&c.tets[u].n)), w.cl[ci]);
+      same = same && back >= 0;
+      w.bl_f[i] = (uint8_t)(f | ((back & 3) << 2));
     }
     if (!__all_sync(kFull, same)) {
       release_held(w, lock, held, nc, na, nx);
@@ -577,7 +566,7 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
     // for the partner lookups below
     uint32_t vs[2] = {0, 0};
     for (int i = lane; i < nb; i += 32) {
-      const int ci = w.bl_ci[i], f = w.bl_f[i];
+      const int ci = w.bl_ci[i], f = w.bl_f[i] & 3;
       uint4 v = w.cr[ci].v;
       set4(v, f, p);
       int pos[3];
@@ -621,7 +610,7 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
     // locks, so its boundary is a closed surface); a lookup that finds no partner is a bug
     bool bad = __any_sync(kFull, vfail);
     for (int i = lane; i < nb && !bad; i += 32) {
-      const int ci = w.bl_ci[i], f = w.bl_f[i];
+      const int ci = w.bl_ci[i], f = w.bl_f[i] & 3, back = w.bl_f[i] >> 2;
       uint4 v = w.cr[ci].v;
       const uint32_t out = get4(w.cr[ci].n, f);
       set4(v, f, p);
@@ -651,14 +640,14 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
       }
       uint4 n4;
       set4(n4, f, out);
-      set4(n4, a, 4u * w.slot[ea >> 2] + (ea & 3u));
-      set4(n4, b, 4u * w.slot[eb >> 2] + (eb & 3u));
-      set4(n4, cc, 4u * w.slot[ec >> 2] + (ec & 3u));
+      set4(n4, a, w.slot[ea >> 2]);
+      set4(n4, b, w.slot[eb >> 2]);
+      set4(n4, cc, w.slot[ec >> 2]);
       const uint32_t s = w.slot[i];
       uint4* dst = reinterpret_cast<uint4*>(c.tets + s);
       __stcg(dst, v);
       __stcg(dst + 1, n4);
-      __stcg(reinterpret_cast<uint32_t*>(&c.tets[out >> 2].n) + (out & 3u), 4u * s + (uint32_t)f);
+      __stcg(reinterpret_cast<uint32_t*>(&c.tets[out].n) + back, s);
     }
     if (__any_sync(kFull, bad)) {
       if (lane == 0) raise_error(c.st, kErrInternal, 0xA8u);

@@ -2,7 +2,10 @@
 //
 // Tetrahedron store (Section 2.2, adapted for coalesced 32-byte sectors): one record of
 //   v[4]  vertex ids (vertex id = position in the insertion order; kGhost for the ghost vertex)
-//   n[4]  neighbour slots packed as 4*t + facet (facet i is opposite vertex i, Fig. 2)
+//   n[4]  neighbour slots (facet i is opposite vertex i, Fig. 2): n[i] is the tetrahedron
+//         across facet i. Which of its facets faces back is not stored: it is the one whose
+//         neighbour is this tetrahedron (two tetrahedra share at most one facet), so ids use
+//         all 32 bits and a mesh may hold up to kMaxSlots records.
 // Both halves of a record share one 32-byte DRAM sector, so a cavity test reads one sector.
 // A dead slot has v.x == v.y (a live tetrahedron never repeats a vertex) and keeps in n.x the
 // id of a tetrahedron created when it died (a redirect for stale walk hints).
@@ -15,6 +18,9 @@ namespace dtg {
 constexpr uint32_t kGhost = 0xFFFFFFFFu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kDeadMark = 0xFFFFFFFEu;
+// Largest number of tetrahedron slots of one mesh: below the two markers above, with room for a
+// grid-stride loop over the slots to step past the end without wrapping 32 bits.
+constexpr uint64_t kMaxSlots = 0xF0000000ull;
 
 // A vertex: coordinates and, in .w, its input index (the order of the perturbation).
 struct __align__(32) Pt {
@@ -92,6 +98,11 @@ __device__ __forceinline__ void set4(uint4& a, int i, uint32_t x) {
   else if (i == 1) a.y = x;
   else if (i == 2) a.z = x;
   else a.w = x;
+}
+
+// The facet of a tetrahedron (neighbour ids n) whose neighbour is t, or -1.
+__device__ __forceinline__ int back_facet(const uint4& n, uint32_t t) {
+  return n.x == t ? 0 : n.y == t ? 1 : n.z == t ? 2 : n.w == t ? 3 : -1;
 }
 
 __device__ __forceinline__ Tet load_tet(const Tet* T, uint32_t t) {

@@ -594,6 +594,66 @@ __global__ void k_collect(const Tet* __restrict__ tets, uint64_t nslots, const P
   }
 }
 
+// Certificate of a mesh (the Delaunay lemma: a closed, consistently oriented complex whose every
+// facet is locally Delaunay is the Delaunay triangulation; with the perturbation of the
+// insertion predicates it is the unique one). One thread per slot; out[0] live finite
+// tetrahedra, out[1] facets whose neighbour is not live or does not share them back, out[2]
+// finite tetrahedra not positively oriented, out[3] facets whose neighbour's opposite vertex is
+// in conflict with the tetrahedron (Section 2.6 for ghosts), out[4] distinct finite vertices.
+__global__ void k_check(Ctx c, uint64_t nslots, uint8_t* seen, unsigned long long* out) {
+  unsigned long long live = 0, bad_adj = 0, bad_orient = 0, bad_del = 0;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nslots;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const Tet T = load_tet(c.tets, (uint32_t)t);
+    if (tet_dead(T.v)) continue;
+    if (!tet_sane(c, T)) {
+      bad_adj += 4;
+      continue;
+    }
+    const bool finite = ghost_pos(T.v) < 0;
+    if (finite) {
+      ++live;
+      PtF F[4];
+      for (int k = 0; k < 4; ++k) {
+        F[k] = load_ptf(c.ptf, get4(T.v, k));
+        seen[get4(T.v, k)] = 1;
+      }
+      if (orient_replace(c, T.v, 0, T.v.x, F[0], F[0], F[1], F[2], F[3]) <= 0) ++bad_orient;
+    }
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t u = get4(T.n, i);
+      const Tet U = load_tet(c.tets, u);
+      const int k = tet_dead(U.v) ? -1 : back_facet(U.n, (uint32_t)t);
+      bool same = k >= 0;
+      for (int j = 0; j < 4 && same; ++j) {
+        if (j == i) continue;
+        const uint32_t x = get4(T.v, j);
+        bool found = false;
+        for (int m = 0; m < 4; ++m) found = found || (m != k && get4(U.v, m) == x);
+        same = found;
+      }
+      if (!same) {
+        ++bad_adj;
+        continue;
+      }
+      const uint32_t q = get4(U.v, k);
+      if (q == kGhost) continue;  // the vertex at infinity lies outside every finite sphere
+      if (in_conflict(c, (uint32_t)t, q, load_ptf(c.ptf, q))) ++bad_del;
+    }
+  }
+  if (live) atomicAdd(&out[0], live);
+  if (bad_adj) atomicAdd(&out[1], bad_adj);
+  if (bad_orient) atomicAdd(&out[2], bad_orient);
+  if (bad_del) atomicAdd(&out[3], bad_del);
+}
+
+__global__ void k_count_seen(const uint8_t* seen, uint64_t n, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    m += seen[i];
+  if (m) atomicAdd(out, m);
+}
+
 __global__ void k_split_keys(const uint4* tets, uint64_t T, uint64_t* khi, uint64_t* klo, uint32_t* idx) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < T;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -1047,7 +1107,7 @@ int reserve_points(dt_handle* h, uint64_t total) {
 int reserve_tets(dt_handle* h, uint64_t total_pts) {
   double f = h->cfg.tet_capacity_factor > 0 ? h->cfg.tet_capacity_factor : 8.0;
   uint64_t need = (uint64_t)(f * (double)total_pts) + 4096;
-  if (need > 0x3FFFFFFFull) need = 0x3FFFFFFFull;  // 4t + facet fits 32 bits
+  if (need > kMaxSlots) need = kMaxSlots;
   if (need <= h->cap_tets) return DT_OK;
   unsigned long long bump = h->has_mesh ? h->st_host->bump : 0;
   if (grow(h->tets, bump, need, h->stream) != cudaSuccess) return DT_ENOMEM;
@@ -1821,7 +1881,7 @@ int batch_impl(dt_handle* h, const double* xyz, const uint64_t* off, uint32_t nc
     T += cap;
     hash = (hash ^ n) * 1099511628211ull;
   }
-  if (T > 0x3FFFFFFFull) return DT_ENOMEM;  // 4 t + facet must fit 32 bits
+  if (T > kMaxSlots) return DT_ENOMEM;
   int rc = batch_reserve(h, N, nc, T);
   if (rc != DT_OK) return rc;
   if (!h->bs) {
@@ -2278,6 +2338,45 @@ int dt_get_points(dt_handle* h, double* xyz_dev, uint64_t rows, uint64_t* n_poin
   int rc = points_out(h->pts, h->n_pts, xyz_dev, rows, h->stream);
   if (rc != DT_OK) return rc;
   return cudaStreamSynchronize(h->stream) == cudaSuccess ? DT_OK : DT_ECUDA;
+}
+
+int dt_check(dt_handle* h, uint64_t* out_host) {
+  if (!h || !out_host) return DT_EINVAL;
+  for (int k = 0; k < 5; ++k) out_host[k] = 0;
+  if (h->batch_mode) return DT_ESTATE;
+  if (!h->has_mesh) return DT_OK;
+  cudaStream_t s = h->stream;
+  int rc = sync_state(h);
+  if (rc != DT_OK) return rc;
+  const uint64_t slots = h->st_host->bump;
+  // the predicates count their exact calls and report errors through a DevState: a scratch one
+  // keeps the handle's statistics those of its insertions
+  char* mem = nullptr;
+  const size_t off_out = (sizeof(DevState) + 15) & ~size_t(15), off_seen = off_out + 64;
+  if (cudaMalloc(&mem, off_seen + std::max<uint64_t>(h->n_pts, 1)) != cudaSuccess) return DT_ENOMEM;
+  cudaMemsetAsync(mem, 0, off_seen + h->n_pts, s);
+  Ctx c = make_ctx(h);
+  c.st = reinterpret_cast<DevState*>(mem);
+  unsigned long long* out = reinterpret_cast<unsigned long long*>(mem + off_out);
+  uint8_t* seen = reinterpret_cast<uint8_t*>(mem + off_seen);
+  if (slots) {
+    k_check<<<grid_for(slots, 256), 256, 0, s>>>(c, slots, seen, out);
+    k_count_seen<<<grid_for(h->n_pts, 256), 256, 0, s>>>(seen, h->n_pts, out + 4);
+    g_kernel_launches += 2;
+  }
+  unsigned long long r[5] = {0, 0, 0, 0, 0};
+  unsigned int err = 0;
+  cudaMemcpyAsync(r, out, sizeof(r), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&err, &c.st->error, 4, cudaMemcpyDeviceToHost, s);
+  rc = cudaStreamSynchronize(s) == cudaSuccess ? DT_OK : DT_ECUDA;
+  cudaFree(mem);
+  if (rc != DT_OK) return rc;
+  for (int k = 0; k < 5; ++k) out_host[k] = r[k];
+  if (err != 0) {
+    h->last_dev_error = err;
+    return map_dev_error(err);
+  }
+  return DT_OK;
 }
 
 int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n) {

@@ -89,7 +89,7 @@ __device__ __forceinline__ bool tet_sane(const Ctx& c, const Tet& T) {
   bool ok = true;
   for (int k = 0; k < 4; ++k) {
     uint32_t v = get4(T.v, k), n = get4(T.n, k);
-    ok = ok && (v == kGhost || v < c.npts) && (n >> 2) < c.ntets;
+    ok = ok && (v == kGhost || v < c.npts) && n < c.ntets;
   }
   return ok;
 }
@@ -110,7 +110,7 @@ struct CavWS {
   uint32_t hmask;
   uint32_t* clist;
   uint32_t cmax;
-  uint32_t* blist;  // boundary facets as 4 * (cavity tetrahedron) + facet
+  uint32_t* blist;  // boundary facets as 4 * (position of the cavity tetrahedron in clist) + facet
   uint32_t bmax;
 };
 
@@ -120,7 +120,7 @@ struct InsWS {
   uint4* nn;  // neighbours of the new tetrahedra, validated before anything is written
   uint32_t* outh;
   uint32_t* slot;
-  uint8_t* ipos;
+  uint8_t* ipos;  // facet of new tetrahedron i on the boundary | 4 * the outside tetrahedron's facet
   uint32_t* vkey;  // 32-slot vertex hash: slot = cavity-local vertex index
   uint16_t* tab;   // 32 x 32 edge table: 4 * (new tetrahedron) + facet
   unsigned long long* ekey;
@@ -212,7 +212,7 @@ static __device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32
   }
   int g = ghost_pos(T.v);
   if (g >= 0) {  // a ghost start steps into its real neighbour (Section 2.6)
-    t = get4(T.n, g) >> 2;
+    t = get4(T.n, g);
     T = tet_at(c, t);
     if (!tet_sane(c, T)) {
       raise_error(c.st, kErrInternal, 0xA001u);
@@ -231,7 +231,7 @@ static __device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32
     int s0 = (salt + steps) & 3;
     for (int k = 0; k < 4; ++k) {
       int i = (s0 + k) & 3;
-      uint32_t nb = get4(T.n, i) >> 2;
+      uint32_t nb = get4(T.n, i);
       if (nb == prev) continue;  // p is on this tetrahedron's side of the facet just crossed
       if (orient_replace(c, T.v, i, p, FP, F0, F1, F2, F3) < 0) {
         exit = i;
@@ -257,7 +257,7 @@ static __device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32
       return kCandWalkLimit;
     }
     prev = t;
-    t = get4(T.n, exit) >> 2;
+    t = get4(T.n, exit);
     T = tet_at(c, t);
     ++steps;
     if (!tet_sane(c, T) || tet_dead(T.v)) {
@@ -308,7 +308,7 @@ static __device__ bool in_conflict(const Ctx& c, uint32_t u, uint32_t p, const P
     o = orient3d(r[0], r[1], r[2], r[3], c.st);
   }
   if (o != 0) return o > 0;
-  uint32_t rr = get4(U.n, g) >> 2;
+  uint32_t rr = get4(U.n, g);
   Tet R = tet_at(c, rr);
   if (!tet_sane(c, R) || ghost_pos(R.v) >= 0) {
     raise_error(c.st, kErrInternal, 0xB001u);
@@ -378,10 +378,11 @@ static __device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uin
     int batch = min(8, nc - head);
     int k = lane >> 2, f = lane & 3;
     bool active = k < batch;
+    const int ci = head + k;
     uint32_t t = 0, u = kNone;
     if (active) {
-      t = vld(&w.clist[head + k]);
-      u = nbr_at(c, t, f) >> 2;
+      t = vld(&w.clist[ci]);
+      u = nbr_at(c, t, f);
       if (u >= c.ntets) {
         raise_error(c.st, kErrInternal, 0xC000u);
         u = t;
@@ -419,7 +420,7 @@ static __device__ int cavity_warp(const Ctx& c, const CavWS& w, uint32_t t0, uin
     unsigned mB = __ballot_sync(kFull, addB);
     if (addB) {
       int pos = nb + __popc(mB & lanemask_lt());
-      if (pos < (int)w.bmax) w.blist[pos] = 4 * t + f;
+      if (pos < (int)w.bmax) w.blist[pos] = 4u * (uint32_t)ci + (uint32_t)f;
     }
     nb += __popc(mB);
     flag = __reduce_or_sync(kFull, myflag);
@@ -486,21 +487,25 @@ static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsi
   if (!__all_sync(kFull, ok)) return kCandLost;
   for (int i = lane; i < nb; i += 32) {
     uint32_t e = vld(&blist[i]);
-    uint32_t t = e >> 2;
+    uint32_t t = vld(&clist[e >> 2]);
     int f = (int)(e & 3u);
     Tet T = load_tet_cg(c.tets, t);
     uint32_t out = get4(T.n, f);
-    if ((out >> 2) >= c.ntets || !tet_sane(c, T)) {
+    if (out >= c.ntets || !tet_sane(c, T)) {
       raise_error(c.st, kErrInternal, 0xD000u);
       ok = false;
       out = 0;
     }
-    if (__ldcg(&c.claim[2 * (size_t)(out >> 2) + 1]) >= prio) ok = false;
+    if (__ldcg(&c.claim[2 * (size_t)out + 1]) >= prio) ok = false;
+    // the facet of the outside tetrahedron that faces t (read before this warp writes anything;
+    // a winner's outside tetrahedra are its own for the round)
+    const int back = back_facet(__ldcg(reinterpret_cast<const uint4*>(&c.tets[out].n)), t);
+    if (back < 0) ok = false;
     uint4 v = T.v;
     set4(v, f, p);
     w.nv[i] = v;
     w.outh[i] = out;
-    w.ipos[i] = (uint8_t)f;
+    w.ipos[i] = (uint8_t)(f | ((back & 3) << 2));
   }
   if (!__all_sync(kFull, ok)) return kCandLost;
   // slots: cavity slots first (Section 2.5), then the allocator (Section 3.6)
@@ -529,7 +534,7 @@ static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsi
     for (int i = lane; i < nb; i += 32) {
       uint4 v = w.nv[i];
       int a, b, cc;
-      after_pos(w.ipos[i], a, b, cc);
+      after_pos(w.ipos[i] & 3, a, b, cc);
       int la = vslot(w.vkey, get4(v, a)), lb = vslot(w.vkey, get4(v, b)), lc = vslot(w.vkey, get4(v, cc));
       if (la < 0 || lb < 0 || lc < 0) {
         vfail = true;
@@ -548,7 +553,7 @@ static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsi
     for (int i = lane; i < nb; i += 32) {
       uint4 v = w.nv[i];
       int pos[3];
-      after_pos(w.ipos[i], pos[0], pos[1], pos[2]);
+      after_pos(w.ipos[i] & 3, pos[0], pos[1], pos[2]);
       for (int k = 0; k < 3; ++k) {
         uint32_t x = get4(v, pos[(k + 1) % 3]), y = get4(v, pos[(k + 2) % 3]);
         unsigned long long key = ((unsigned long long)min(x, y) << 32) | max(x, y);
@@ -571,7 +576,7 @@ static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsi
   bool bad = false;
   for (int i = lane; i < nb; i += 32) {
     uint4 v = w.nv[i];
-    int ip = w.ipos[i];
+    int ip = w.ipos[i] & 3;
     int a, b, cc;
     after_pos(ip, a, b, cc);
     uint32_t ea, eb, ec;
@@ -597,9 +602,9 @@ static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsi
     }
     uint4 nn;
     set4(nn, ip, w.outh[i]);
-    set4(nn, a, 4u * vld(&w.slot[ea >> 2]) + (ea & 3u));
-    set4(nn, b, 4u * vld(&w.slot[eb >> 2]) + (eb & 3u));
-    set4(nn, cc, 4u * vld(&w.slot[ec >> 2]) + (ec & 3u));
+    set4(nn, a, vld(&w.slot[ea >> 2]));
+    set4(nn, b, vld(&w.slot[eb >> 2]));
+    set4(nn, cc, vld(&w.slot[ec >> 2]));
     w.nn[i] = nn;
   }
   if (__any_sync(kFull, bad)) {
@@ -614,7 +619,7 @@ static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsi
     dst[0] = w.nv[i];
     dst[1] = w.nn[i];
     uint32_t out = w.outh[i];
-    reinterpret_cast<uint32_t*>(&c.tets[out >> 2].n)[out & 3u] = 4u * s + (uint32_t)w.ipos[i];
+    reinterpret_cast<uint32_t*>(&c.tets[out].n)[w.ipos[i] >> 2] = s;
   }
   // cavity slots left over (|C| > |B|) die and join the free list after the round
   int freed = nc - nb;
@@ -792,7 +797,7 @@ static __device__ bool init_mesh(const Ctx& c, uint32_t vbegin, uint32_t vend, u
               }
           }
           if (match == 3) {
-            nn[t][f] = 4u * (tbase + u) + g;
+            nn[t][f] = tbase + u;
             break;
           }
         }

@@ -4,7 +4,9 @@
   (1e7 uniform, 1e7 degenerate mix, 1e8 uniform, 1e8 cube + slab) hashes to the SHA-256 the serial
   CPU oracle's list of the same seeded input hashes to (tests/golden/fullsize.json, written by
   tests/golden/make_fullsize.py, which calls only the oracle). On a mismatch the per-chunk digests
-  locate the first differing block of rows.
+  locate the first differing block of rows. The device certificate (dt_check) of each mesh is
+  checked too: no faults, and its counts equal the oracle's.
+* Beyond 2^30 tetrahedra: 2e8 uniform points, certified on the device.
 * The bench's workload (1e7 uniform points, seed 2) is also checked by what holds at any size:
   every facet is shared by at most two tetrahedra, the triangulation is a topological ball
   (Euler characteristic 1), and sampled tetrahedra are positively oriented with an empty
@@ -41,7 +43,10 @@ def test_fullsize_canonical_list_matches_the_oracle_digest(name):
         t.insert(torch.from_numpy(x).cuda())
         st = t.stats()
         del x
+        cert = t.check()
         tets = t.tets(canonical=True).cpu().numpy().view(np.uint32)
+    assert cert == {"tets": rec["n_tets"], "bad_adjacency": 0, "bad_orientation": 0, "not_delaunay": 0,
+                    "vertices": rec["n"] - rec["n_dups"]}
     assert st["n_dups"] == rec["n_dups"]
     assert len(tets) == rec["n_tets"]
     t = np.ascontiguousarray(tets, dtype="<u4")
@@ -100,3 +105,27 @@ def test_uniform_1e7_is_a_delaunay_ball():
                 continue
             # exactly: a point strictly inside the sphere of a positive tetrahedron has insphere < 0
             assert oracle.insphere(a, b, c, d, x[i]) >= 0, (v, i)
+
+
+@pytest.mark.parametrize("n", [2 * 10 ** 8])
+def test_beyond_2_pow_30_tetrahedra(n):
+    """2e8 uniform points (1.35e9 tetrahedra, more than 2^30 slots) on one GPU. The oracle's
+    list does not fit the host that writes the digests, so the mesh is certified on the device:
+    reciprocal adjacency, positive orientation, every facet locally Delaunay under the exact
+    perturbed predicates, and every point a vertex."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < 150e9:
+        pytest.skip("needs about 150 GB of free device memory")
+    x = synth.uniform_cube(n, 2)
+    xd = torch.from_numpy(x).cuda()
+    del x
+    with dt.Triangulation(seed=2) as t:
+        t.insert(xd)
+        del xd
+        st = t.stats()
+        cert = t.check()
+    assert st["n_unique"] == n
+    assert cert["tets"] > 2 ** 30 and 6.7 * n < cert["tets"] < 6.8 * n
+    assert cert["bad_adjacency"] == cert["bad_orientation"] == cert["not_delaunay"] == 0
+    assert cert["vertices"] == n
+    assert st["device_bytes"] / n < 640

@@ -198,6 +198,40 @@ def test_schedule_does_not_change_tets():
     assert_same(got, ref)
 
 
+@pytest.mark.parametrize("kind,n,seed", [("uniform", 20000, 8), ("degenerate", 30000, 3), ("slab", 30000, 5),
+                                         ("uniform", 5, 1)])
+def test_certificate_holds_where_the_oracle_agrees(kind, n, seed):
+    """dt_check on meshes equal to the oracle's: every adjacency reciprocal, every finite
+    tetrahedron positively oriented, every facet locally Delaunay under the perturbed predicates,
+    and its counts equal to the oracle's (tetrahedra, distinct vertices)."""
+    x = synth.make(kind, n, seed)
+    ref, ost = oracle.delaunay(x, seed=seed)
+    with dt.Triangulation(seed=seed) as t:
+        t.insert(torch.from_numpy(x).cuda())
+        cert = t.check()
+        got = t.tets_numpy(canonical=True)
+        st = t.stats()
+    assert_same(got, ref)
+    assert cert == {"tets": len(ref), "bad_adjacency": 0, "bad_orientation": 0, "not_delaunay": 0,
+                    "vertices": ost["n_unique"]}
+    assert st["n_unique"] == ost["n_unique"]
+
+
+@pytest.mark.parametrize("name", sorted(DEGENERATE_SETS))
+def test_certificate_on_degenerate_sets(name):
+    x = DEGENERATE_SETS[name]
+    ref, ost = oracle.delaunay(x)
+    with dt.Triangulation() as t:
+        t.insert(torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda())
+        before = t.stats()
+        cert = t.check()
+        after = t.stats()
+    assert cert["bad_adjacency"] == cert["bad_orientation"] == cert["not_delaunay"] == 0
+    assert cert["tets"] == len(ref) and cert["vertices"] == ost["n_unique"]
+    before.pop("n_launches"), after.pop("n_launches")  # the check's own two launches count
+    assert before == after  # the check leaves the handle's statistics alone
+
+
 def test_successive_inserts_extend_the_triangulation():
     x = synth.uniform_cube(12000, 17)
     x[11000:11010] = x[100:110]  # duplicates across calls keep the earlier (smaller) index

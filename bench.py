@@ -9,7 +9,9 @@ library's stream; `e2e` repeats the step through the host entry points with the 
 Multi-GPU runs are replicas (one independent cloud per rank; a single cloud does not shard).
 The default line also carries the CPU legs (the serial oracle, and the paper's CPU thread scheme
 on every host core, both on the first 1e6 points) and the other rows of the path: the batched
-form, the learned schedule against the plain one, and Delaunay refinement of a box.
+form, the learned schedule against the plain one, Delaunay refinement of a box, 1e8 and 3e8
+uniform points (the latter beyond 2^30 tetrahedra, certified on the device by dt_check), and the
+sub-determinant caching ablation on the default workload.
 """
 from __future__ import annotations
 
@@ -669,6 +671,68 @@ def scale_run(kind, n, seed, steps, warmup):
             "bit_exact_full": exact, "digest_of": name, "device_bytes_per_point": st["device_bytes"] / n}
 
 
+def scale_certified(n, seed, steps, warmup):
+    """A workload beyond what the oracle's digests cover (more than 2^30 tetrahedra): Mtets/s over
+    `steps` timed steps and the device certificate of the last mesh (dt_check: reciprocal
+    adjacency, positive orientation, every facet locally Delaunay under the exact perturbed
+    predicates, every point a vertex)."""
+    import torch
+    import paper_1805_08831_gb300 as dt
+    x = synth.uniform_cube(int(n), seed)
+    xd = torch.from_numpy(x).cuda()
+    del x
+    stream = torch.cuda.current_stream()
+    tri = dt.Triangulation(seed=SEED, stream=stream)
+    for _ in range(warmup):
+        tri.clear()
+        tri.insert(xd)
+    ms, st = timed_steps(tri, xd, steps, stream)
+    del xd
+    cert = tri.check()
+    tri.close()
+    torch.cuda.empty_cache()
+    t = sum(ms) / len(ms)
+    return {"workload": f"{int(n):.0e} points i.i.d. uniform in the unit cube, float64, seed {seed}",
+            "value": cert["tets"] / (t / 1e3) / 1e6, "unit": "Mtets/s", "ms_per_step": t, "steps": steps,
+            "tets": cert["tets"], "certificate": cert,
+            "certified": cert["bad_adjacency"] == cert["bad_orientation"] == cert["not_delaunay"] == 0
+            and cert["vertices"] == st["n_unique"],
+            "device_bytes_per_point": st["device_bytes"] / n, "paper_bytes_per_vertex": 332}
+
+
+def subdet_ablation(n, seed, steps, warmup, plain_value):
+    """The sub-determinant cache of Section 2.4 as an ablation (DT_SUBDET=1: the asynchronous
+    engine's conflict tests read cached cofactors, re-checked under the locks) on the default
+    workload: Mtets/s, the ratio to the line's plain value, and the bit-exact flag."""
+    import torch
+    import paper_1805_08831_gb300 as dt
+    x = synth.make("uniform", int(n), seed)
+    xd = torch.from_numpy(x).cuda()
+    del x
+    stream = torch.cuda.current_stream()
+    os.environ["DT_SUBDET"] = "1"
+    try:
+        tri = dt.Triangulation(seed=SEED, stream=stream)
+    finally:
+        del os.environ["DT_SUBDET"]
+    for _ in range(warmup):
+        tri.clear()
+        tri.insert(xd)
+    ms, st = timed_steps(tri, xd, steps, stream)
+    T = tri.num_tets()
+    name = golden_name("uniform", n, seed)
+    exact = digest_check(tri, name) if name else None
+    tri.close()
+    del xd
+    torch.cuda.empty_cache()
+    t = sum(ms) / len(ms)
+    v = T / (t / 1e3) / 1e6
+    return {"workload": workload_name("uniform", n), "value": v, "unit": "Mtets/s", "ms_per_step": t,
+            "cached_over_plain": v / plain_value, "n_restarts": st["n_restarts"],
+            "n_exact_handoff": st["n_exact_handoff"], "device_bytes_per_point": st["device_bytes"] / n,
+            "bit_exact_full": exact}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -816,6 +880,8 @@ def main():
                          "shape": [bl["config"]["batch_warps"], bl["config"]["batch_min_blocks"],
                                    bl["config"]["batch_alpha"]], "graph_replay": bl["config"]["graph_replay"]}
         line["scale_1e8"] = scale_run("uniform", 1e8, SEED, 2, 1)
+        line["scale_3e8"] = scale_certified(3e8, SEED, 1, 1)
+        line["ablation_subdet"] = subdet_ablation(n, SEED, args.steps, args.warmup, value)
         line["learned"], _ = learned_vs_plain(1e8, 2, 1, args.train_steps, seed=5)
         line["refine"] = refine_run(REFINE_K, 3, 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

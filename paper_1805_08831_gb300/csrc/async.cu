@@ -76,9 +76,10 @@ struct AWSTail<false, kHashN, kFMaxN> {
 // tetrahedra with their vertices as read, the boundary facets, the ball's slots, a private pool
 // of free slots, deferred points, and the warp's state (uniform across its lanes, written by
 // lane 0). Held: the type of a lane's lock mask (one bit per lock-list entry of the lane).
-template <int kHashN, int kCMaxN, int kAMaxN, int kFMaxN, bool kTableB, class HeldT>
+template <int kHashN, int kCMaxN, int kAMaxN, int kFMaxN, bool kTableB, class HeldT, bool kCacheB>
 struct AWS : AWSTail<kTableB, kHashN, kFMaxN> {
   static constexpr int kHash = kHashN, kCMax = kCMaxN, kAMax = kAMaxN, kFMax = kFMaxN;
+  static constexpr bool kCache = kCacheB;  // conflict tests through the sub-determinant cache
   static constexpr int kPool = kFMaxN + 36;  // a refill of 32 slots always fits below kFMax
   static constexpr bool kTable = kTableB;
   using Held = HeldT;
@@ -105,8 +106,11 @@ struct AWS : AWSTail<kTableB, kHashN, kFMaxN> {
 
 // Shared-memory workspace of the main kernel (cavities of up to 64 tetrahedra and 60 boundary
 // facets) and the global-memory one of the large-cavity kernel.
-using SmallWS = AWS<256, 64, 64, 60, true, unsigned>;
-using LargeWS = AWS<4096, 640, 704, 704, false, unsigned long long>;
+template <bool kCache>
+using SmallWST = AWS<256, 64, 64, 60, true, unsigned, kCache>;
+template <bool kCache>
+using LargeWST = AWS<4096, 640, 704, 704, false, unsigned long long, kCache>;
+using LargeWS = LargeWST<false>;  // the same layout with and without the cache
 
 __device__ __forceinline__ Tet ld_tet(const Tet* T, uint32_t t) { return load_tet_cg(T, t); }
 
@@ -158,6 +162,76 @@ __device__ __forceinline__ int orient_with_p(const Ctx& c, int i, const PtF& FP,
 __device__ __forceinline__ int inside_async(const Ctx& c, const uint4& v, const PtF& FP) {
   PtF A = load_ptf(c.ptf, v.x), B = load_ptf(c.ptf, v.y), C = load_ptf(c.ptf, v.z), D = load_ptf(c.ptf, v.w);
   return insphere_f(A, B, C, D, FP, c.eta);
+}
+
+// Sub-determinant cache (Section 2.4; an ablation, off unless the handle allocates it). With
+// b, c, d, e the differences of the tetrahedron's other vertices and of p from its first vertex
+// a, the insphere determinant expanded along e's row is ex Ax + ey Ay + ez Az + |e|^2 AL, and
+// the cofactors A depend on the tetrahedron alone. Two float4 per slot: q0 = (Ax, Ay, Az, AL);
+// q1 = (the permanents of Ax and Ay, then of Az and AL, each pair as two bfloat16 rounded up;
+// the largest |coordinate| of b, c, d; 1 when the entry is valid). The same monomials as
+// insphere_f's with fewer roundings on each (12 against 16), so insphere_f's bound holds;
+// rounding the permanents up widens it by at most 2^-7 of itself.
+__device__ __forceinline__ uint32_t bf16_up(float x) {  // x >= 0: the bfloat16 at or above x
+  return (__float_as_uint(x) + 0xFFFFu) >> 16;
+}
+__device__ __forceinline__ float bf16_lo(float packed) { return __uint_as_float(__float_as_uint(packed) << 16); }
+__device__ __forceinline__ float bf16_hi(float packed) {
+  return __uint_as_float(__float_as_uint(packed) & 0xFFFF0000u);
+}
+
+__device__ __forceinline__ void subdet_make(const PtF& A, const PtF& B, const PtF& C, const PtF& D, float4& q0,
+                                            float4& q1) {
+  float bx, by, bz, cx, cy, cz, dx, dy, dz;
+  diff_f(B, A, bx, by, bz);
+  diff_f(C, A, cx, cy, cz);
+  diff_f(D, A, dx, dy, dz);
+  const float Lb = bx * bx + by * by + bz * bz, Lc = cx * cx + cy * cy + cz * cz, Ld = dx * dx + dy * dy + dz * dz;
+  const float cd0 = cy * dz - cz * dy, cd1 = cx * dz - cz * dx, cd2 = cx * dy - cy * dx;
+  const float bd0 = by * dz - bz * dy, bd1 = bx * dz - bz * dx, bd2 = bx * dy - by * dx;
+  const float bc0 = by * cz - bz * cy, bc1 = bx * cz - bz * cx, bc2 = bx * cy - by * cx;
+  const float pcd0 = fabsf(cy * dz) + fabsf(cz * dy), pcd1 = fabsf(cx * dz) + fabsf(cz * dx),
+              pcd2 = fabsf(cx * dy) + fabsf(cy * dx);
+  const float pbd0 = fabsf(by * dz) + fabsf(bz * dy), pbd1 = fabsf(bx * dz) + fabsf(bz * dx),
+              pbd2 = fabsf(bx * dy) + fabsf(by * dx);
+  const float pbc0 = fabsf(by * cz) + fabsf(bz * cy), pbc1 = fabsf(bx * cz) + fabsf(bz * cx),
+              pbc2 = fabsf(bx * cy) + fabsf(by * cx);
+  q0.x = Lc * bd0 - Lb * cd0 - Ld * bc0;
+  q0.y = Lb * cd1 + Ld * bc1 - Lc * bd1;
+  q0.z = Lc * bd2 - Lb * cd2 - Ld * bc2;
+  q0.w = bx * cd0 - by * cd1 + bz * cd2;
+  const float px = Lc * pbd0 + Lb * pcd0 + Ld * pbc0, py = Lc * pbd1 + Lb * pcd1 + Ld * pbc1,
+              pz = Lc * pbd2 + Lb * pcd2 + Ld * pbc2;
+  const float pl = fabsf(bx) * pcd0 + fabsf(by) * pcd1 + fabsf(bz) * pcd2;
+  q1.x = __uint_as_float(bf16_up(px) | (bf16_up(py) << 16));
+  q1.y = __uint_as_float(bf16_up(pz) | (bf16_up(pl) << 16));
+  q1.z = fmaxf(fmaxf(fmaxf(fabsf(bx), fabsf(by)), fmaxf(fabsf(bz), fabsf(cx))),
+               fmaxf(fmaxf(fabsf(cy), fabsf(cz)), fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fabsf(dz))));
+  q1.w = 1.f;
+}
+
+// insphere_f of the cached tetrahedron (first vertex A) and p: -1 inside, 1 outside, 0 undecided.
+__device__ __forceinline__ int insphere_cached(const float4& q0, const float4& q1, const PtF& A, const PtF& FP,
+                                               float eta) {
+  float ex, ey, ez;
+  diff_f(FP, A, ex, ey, ez);
+  const float Le = ex * ex + ey * ey + ez * ez;
+  const float det = (ex * q0.x + ey * q0.y) + (ez * q0.z + Le * q0.w);
+  const float perm = (fabsf(ex) * bf16_lo(q1.x) + fabsf(ey) * bf16_hi(q1.x)) +
+                     (fabsf(ez) * bf16_lo(q1.y) + Le * bf16_hi(q1.y));
+  const float mm = fmaxf(q1.z, fmaxf(fabsf(ex), fmaxf(fabsf(ey), fabsf(ez)))) + eta, mm2 = mm * mm;
+  const float eb = kInsphereCf * perm + 400.0f * eta * (mm2 * mm2);
+  if (!(perm > 1e-30f && perm < 1e30f)) return 0;
+  return det > eb ? 1 : (det < -eb ? -1 : 0);
+}
+
+// The conflict test of a finite tetrahedron u (vertices v) through the cache when its entry
+// is valid, else from the coordinates.
+__device__ __forceinline__ int inside_maybe_cached(const Ctx& c, uint32_t u, const uint4& v, const PtF& FP) {
+  const float4 q1 = __ldcg(c.subdet + 2 * (size_t)u + 1);
+  if (q1.w == 0.f) return inside_async(c, v, FP);
+  const float4 q0 = __ldcg(c.subdet + 2 * (size_t)u);
+  return insphere_cached(q0, q1, load_ptf(c.ptf, v.x), FP, c.eta);
 }
 
 // Visibility walk (Section 2.1, ghost rules of Section 2.6) on unlocked reads. Lanes 0-3 test
@@ -241,10 +315,11 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
 // Conflict of a record U (already read) with p: 1 in the cavity, 0 outside, -2 undecided by the
 // FP32 stage. For a ghost whose hull facet's plane holds p the finite neighbour across the facet
 // decides (Section 2.6): that case is left to the round-based engine (-2).
-__device__ __forceinline__ int conflict_async(const Ctx& c, const Tet& U, const PtF& FP) {
+template <bool kCache>
+__device__ __forceinline__ int conflict_async(const Ctx& c, uint32_t u, const Tet& U, const PtF& FP) {
   const int g = ghost_pos(U.v);
   if (g < 0) {
-    const int s = inside_async(c, U.v, FP);
+    const int s = kCache ? inside_maybe_cached(c, u, U.v, FP) : inside_async(c, U.v, FP);
     return s < 0 ? 1 : (s > 0 ? 0 : -2);
   }
   // orientation of the hull facet's three vertices and p in the ghost's place
@@ -329,7 +404,7 @@ __device__ __forceinline__ int cavity_async(const Ctx& c, W& w, uint32_t t0, uin
     Tet U;
     if (is_leader) {
       U = ld_tet(c.tets, u);
-      const int in = (tet_dead(U.v) || !rec_ok(U, c.ntets, c.npts)) ? -1 : conflict_async(c, U, FP);
+      const int in = (tet_dead(U.v) || !rec_ok(U, c.ntets, c.npts)) ? -1 : conflict_async<W::kCache>(c, u, U, FP);
       if (in == -2) {
         myflag |= 4;
       } else if (in < 0) {
@@ -544,6 +619,18 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
       same = same && back >= 0;
       w.bl_f[i] = (uint8_t)(f | ((back & 3) << 2));
     }
+    if constexpr (W::kCache) {
+      // the cache's decisions were taken on entries read without locks: each is taken again on
+      // the entry as it stands under the locks (an entry changes only with its record)
+      for (int i = lane; i < nc; i += 32) {
+        const uint4 v = w.cr[i].v;
+        if (ghost_pos(v) < 0) same = same && inside_maybe_cached(c, w.cl[i], v, FP) < 0;
+      }
+      for (int i = lane; i < na; i += 32) {
+        const uint4 v = w.av[i];
+        if (ghost_pos(v) < 0) same = same && inside_maybe_cached(c, w.al[i], v, FP) > 0;
+      }
+    }
     if (!__all_sync(kFull, same)) {
       release_held(w, lock, held, nc, na, nx);
       if (nx > 0) pool_give(c, w, w.ex, nx);
@@ -647,6 +734,13 @@ __device__ __forceinline__ int try_insert(const Ctx& c, W& w, uint32_t* lock, ui
       uint4* dst = reinterpret_cast<uint4*>(c.tets + s);
       __stcg(dst, v);
       __stcg(dst + 1, n4);
+      if constexpr (W::kCache) {
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;  // a ghost's entry stays invalid
+        if (ghost_pos(v) < 0)
+          subdet_make(load_ptf(c.ptf, v.x), load_ptf(c.ptf, v.y), load_ptf(c.ptf, v.z), load_ptf(c.ptf, v.w), q0, q1);
+        __stcg(c.subdet + 2 * (size_t)s, q0);
+        __stcg(c.subdet + 2 * (size_t)s + 1, q1);
+      }
       __stcg(reinterpret_cast<uint32_t*>(&c.tets[out].n) + back, s);
     }
     if (__any_sync(kFull, bad)) {
@@ -717,7 +811,7 @@ __device__ __noinline__ int try_insert_large(const Ctx& c, const AsyncIO& io, W&
     }
   k = __shfl_sync(kFull, k, 0);
   if (k < 0) return kABig;
-  LargeWS& L = static_cast<LargeWS*>(io.big_ws)[k];
+  LargeWST<W::kCache>& L = static_cast<LargeWST<W::kCache>*>(io.big_ws)[k];
   if (lane == 0) {
     L.fa = w.fa;
     L.bump = w.bump;
@@ -833,10 +927,10 @@ __device__ __forceinline__ void run_segment(const Ctx& c, const AsyncIO& io, W& 
   }
 }
 
-template <int kMinBlocks>
+template <int kMinBlocks, bool kCache = false>
 __global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO io, uint32_t* lock,
                                                                const uint8_t* __restrict__ vflag, InsertLog lg) {
-  __shared__ SmallWS s_ws[kAW];
+  __shared__ SmallWST<kCache> s_ws[kAW];
   const int wid = threadIdx.x >> 5;
   const uint32_t seg = blockIdx.x * kAW + wid;
   if (seg >= io.W) return;
@@ -854,8 +948,9 @@ __global__ void __launch_bounds__(kAW * 32, kMinBlocks) k_async(Ctx c, AsyncIO i
 // Large cavities (beyond the shared-memory workspaces): the same insertion with each warp's
 // workspace in global memory. Owner words are per warp of the launch, and this kernel never
 // runs beside k_async, so warp numbers may repeat across the two.
+template <bool kCache>
 __global__ void __launch_bounds__(128) k_async_big(Ctx c, AsyncIO io, uint32_t* lock, const uint8_t* __restrict__ vflag,
-                                                  InsertLog lg, LargeWS* ws) {
+                                                  InsertLog lg, LargeWST<kCache>* ws) {
   const uint32_t seg = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (seg >= io.W) return;
   const uint64_t b0 = (uint64_t)seg * io.L;
@@ -916,7 +1011,9 @@ int async_launch(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint8_t*
   cc.coherent = 1;
   cc.max_walk = io.max_walk;
   const unsigned blocks = (io.W + kAW - 1) / kAW;
-  switch (async_blocks_per_sm()) {
+  // the sub-determinant cache ablation is built for the default 8 blocks per SM only
+  switch (c.subdet ? 0 : async_blocks_per_sm()) {
+    case 0: k_async<8, true><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
     case 4: k_async<4><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
     case 5: k_async<5><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
     case 6: k_async<6><<<blocks, kAW * 32, 0, s>>>(cc, io, lock, vflag, lg); break;
@@ -937,7 +1034,10 @@ int async_launch_big(const Ctx& c, const AsyncIO& io, uint32_t* lock, const uint
   Ctx cc = c;
   cc.coherent = 1;
   cc.max_walk = io.max_walk;
-  k_async_big<<<(io.W + 3) / 4, 128, 0, s>>>(cc, io, lock, vflag, lg, static_cast<LargeWS*>(ws));
+  if (c.subdet)
+    k_async_big<true><<<(io.W + 3) / 4, 128, 0, s>>>(cc, io, lock, vflag, lg, static_cast<LargeWST<true>*>(ws));
+  else
+    k_async_big<false><<<(io.W + 3) / 4, 128, 0, s>>>(cc, io, lock, vflag, lg, static_cast<LargeWS*>(ws));
   k_async_close_copy<<<152, 256, 0, s>>>(cc);
   k_async_close_state<<<1, 1, 0, s>>>(cc);
   g_kernel_launches += 3;

@@ -880,6 +880,8 @@ struct dt_handle {
   Tet* tets = nullptr;
   unsigned long long* claim = nullptr;
   uint32_t* lock = nullptr;  // asynchronous engine: owner of each slot (0 = free)
+  float4* subdet = nullptr;  // sub-determinant cache (ablation, DT_SUBDET=1): two float4 per slot
+  bool use_subdet = false;
   uint64_t cap_tets = 0;
   uint32_t* freelist = nullptr;
   uint32_t* pending = nullptr;
@@ -908,6 +910,8 @@ struct dt_handle {
   uint64_t last_n = 0;
   double alpha = 0.02;   // candidates per round = alpha * mesh vertices (measured best at 1e7 and 1e8)
   double alpha_refine = 0.01;  // the same during dt_refine
+  double refine_rebuild = 0.25;  // dt_refine: rebuild the mesh when an iteration adds this share
+  bool refine_rebuild_async = true;  // ... and let the rebuild use the asynchronous engine
   double gamma = 0.3;    // wave size = gamma * mesh vertices (round-based and batch engines)
   double gamma_async = 2.0;  // the asynchronous engine's waves (measured: 164.9 ms per 1e7 uniform
                              // step at 2.0 against 166.8 at 1.0, 175.0 at 0.5 and 185.6 at 0.3;
@@ -1048,6 +1052,7 @@ Ctx make_ctx(dt_handle* h) {
   c.coherent = 0;
   c.ntets = (uint32_t)h->cap_tets;
   c.npts = (uint32_t)h->cap_pts;
+  c.subdet = h->use_subdet ? h->subdet : nullptr;
   return c;
 }
 
@@ -1062,6 +1067,7 @@ uint64_t device_bytes(const dt_handle* h) {
   uint64_t b = 0;
   b += h->cap_pts * (sizeof(Pt) + sizeof(PtF) + 1 + 4);             // points, FP32 copy, flag, hint
   b += h->cap_tets * (sizeof(Tet) + 16 + 4);                         // records, claim pair, owner word
+  if (h->subdet) b += h->cap_tets * 2 * sizeof(float4);              // sub-determinant cache
   b += h->cap_free * 8;                                              // free list and pending
   if (h->cell_hint_cb > 0) {
     const int cb = h->cell_hint_cb, cbc = cb > 3 ? cb - 3 : 1;
@@ -1118,6 +1124,11 @@ int reserve_tets(dt_handle* h, uint64_t total_pts) {
   if (grow(h->claim, 2 * bump, 2 * need, h->stream) != cudaSuccess) return DT_ENOMEM;
   // claim words of slots not yet handed out start at zero (below every priority)
   cudaMemsetAsync(h->claim + 2 * bump, 0, 2 * (need - bump) * sizeof(unsigned long long), h->stream);
+  if (h->use_subdet) {
+    // cache entries of slots not yet handed out read as invalid
+    if (grow(h->subdet, 2 * bump, 2 * need, h->stream) != cudaSuccess) return DT_ENOMEM;
+    cudaMemsetAsync(h->subdet + 2 * bump, 0, 2 * (need - bump) * sizeof(float4), h->stream);
+  }
   // owner words: every slot free (no lock is held between launches)
   cudaStreamSynchronize(h->stream);
   cudaFree(h->lock);
@@ -1673,6 +1684,7 @@ int insert_impl(dt_handle* h, const double* xyz, uint64_t n, bool allow_async = 
     cudaMemsetAsync(h->cell_hint2, 0xFF, (size_t)4 << (3 * cbc), s);
     // a new mesh: every slot reads as dead until it is handed out (see reserve_tets)
     cudaMemsetAsync(h->tets, 0, h->cap_tets * sizeof(Tet), s);
+    if (h->subdet) cudaMemsetAsync(h->subdet, 0, 2 * h->cap_tets * sizeof(float4), s);
     DevState z{};
     z.stamp = h->next_stamp;
     z.capacity = h->cap_tets;
@@ -1779,6 +1791,7 @@ Ctx batch_ctx(dt_handle* h) {
   Ctx c = make_ctx(h);
   c.coherent = 1;  // a block reads back the tetrahedra it writes
   c.max_walk = h->cfg.max_walk_steps ? h->cfg.max_walk_steps : kDefaultWalk;
+  c.subdet = nullptr;  // the batch store has no cache
   return c;
 }
 
@@ -2211,6 +2224,8 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   h->stream = (cudaStream_t)h->cfg.stream;
   if (const char* a = std::getenv("DT_ALPHA")) h->alpha = std::atof(a);
   if (const char* a = std::getenv("DT_ALPHA_REFINE")) h->alpha_refine = std::atof(a);
+  if (const char* a = std::getenv("DT_REFINE_REBUILD")) h->refine_rebuild = std::atof(a);
+  if (const char* a = std::getenv("DT_REFINE_REBUILD_ASYNC")) h->refine_rebuild_async = std::atoi(a) != 0;
   if (const char* g = std::getenv("DT_GAMMA")) h->gamma = std::atof(g);
   if (const char* g = std::getenv("DT_GAMMA_ASYNC")) h->gamma_async = std::atof(g);
   if (const char* a = std::getenv("DT_ALPHA_CTA")) h->alpha_cta = std::atof(a);
@@ -2221,6 +2236,7 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   if (const char* a = std::getenv("DT_ASYNC_WARPS")) h->async_warps = std::strtoull(a, nullptr, 10);
   if (const char* a = std::getenv("DT_ASYNC_HANDOFF")) h->async_handoff_frac = std::atof(a);
   if (const char* a = std::getenv("DT_ASYNC_HANDOFF_MIN")) h->async_handoff_min = std::strtoull(a, nullptr, 10);
+  if (const char* a = std::getenv("DT_SUBDET")) h->use_subdet = std::atoi(a) != 0;
   if (const char* a = std::getenv("DT_ASYNC_BALL_START")) h->async_ball_start = (uint32_t)std::atoi(a);
   if (const char* w = std::getenv("DT_WALK_THREADS")) {
     int v = std::atoi(w);
@@ -2240,8 +2256,14 @@ int dt_create(dt_handle** out, const dt_config* cfg) {
   return DT_OK;
 }
 
+int clear_mesh(dt_handle* h, bool keep_stats);
+
 int dt_clear(dt_handle* h) {
   if (!h) return DT_EINVAL;
+  return clear_mesh(h, false);
+}
+
+int clear_mesh(dt_handle* h, bool keep_stats) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   // claim priorities keep growing across triangulations, so stale claims never win
@@ -2265,8 +2287,10 @@ int dt_clear(dt_handle* h) {
   h->last_n = 0;
   h->cmax = 0.0;
   h->last_dev_error = h->last_dev_info = 0;
-  h->stats = dt_stats{};
-  h->launches0 = g_kernel_launches;
+  if (!keep_stats) {
+    h->stats = dt_stats{};
+    h->launches0 = g_kernel_launches;
+  }
   std::memset(h->st_host, 0, sizeof(DevState));
   return cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream) == cudaSuccess ? DT_OK : DT_ECUDA;
 }
@@ -2275,6 +2299,28 @@ int dt_insert(dt_handle* h, const double* xyz_dev, uint64_t n) {
   if (!h || (n > 0 && !xyz_dev)) return DT_EINVAL;
   if (h->batch_mode) return DT_ESTATE;
   return insert_impl(h, xyz_dev, n);
+}
+
+// The mesh of every point the handle holds plus ns more (device, [ns, 3]), built from scratch:
+// the points keep their input indices, so the triangulation (unique under the perturbation) is
+// the one inserting the ns points into the current mesh would give. An iteration of dt_refine
+// that adds many points into a mesh whose interior is empty meets cavities of thousands of
+// tetrahedra; in BRIO order over all points the cavities stay small.
+int rebuild_with(dt_handle* h, const double* extra, uint64_t ns, bool allow_async) {
+  const uint64_t n0 = h->n_pts, N = n0 + ns;
+  double* all = nullptr;
+  if (cudaMalloc(&all, N * 24) != cudaSuccess) return DT_ENOMEM;
+  int rc = points_out(h->pts, n0, all, n0, h->stream);
+  if (rc == DT_OK &&
+      cudaMemcpyAsync(all + 3 * n0, extra, ns * 24, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    rc = DT_ECUDA;
+  const dt_stats keep = h->stats;
+  if (rc == DT_OK) rc = clear_mesh(h, true);
+  h->stats = keep;
+  if (rc == DT_OK) rc = insert_impl(h, all, N, allow_async);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(all);
+  return rc;
 }
 
 int dt_refine(dt_handle* h, double size, double ratio, double spacing, const double* box_host, uint32_t max_iters,
@@ -2320,7 +2366,11 @@ int dt_refine(dt_handle* h, double size, double ratio, double spacing, const dou
     // fill an empty interior (cavities of thousands of tetrahedra): the round-based engine,
     // with its full predicate cascade and large-cavity tiers, is faster here (5.9 s against
     // 10.9 s for the 1/128 box)
-    if ((rc = insert_impl(h, h->rws.xyz, ns, false)) != DT_OK) break;
+    if (h->refine_rebuild > 0 && (double)ns >= h->refine_rebuild * (double)h->n_pts)
+      rc = rebuild_with(h, h->rws.xyz, ns, h->refine_rebuild_async);
+    else
+      rc = insert_impl(h, h->rws.xyz, ns, false);
+    if (rc != DT_OK) break;
     added += ns;
     ++iters;
   }
@@ -2578,6 +2628,7 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->tets);
   cudaFree(h->claim);
   cudaFree(h->lock);
+  cudaFree(h->subdet);
   cudaFree(h->async_big_ws);
   cudaFree(h->async_borrow_ws);
   cudaFree(h->async_borrow_busy);

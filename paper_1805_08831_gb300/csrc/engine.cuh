@@ -58,6 +58,8 @@ struct Ctx {
   int coherent;  // 1 when this kernel also writes the tetrahedra it reads (L2 loads)
   uint32_t ntets;  // tetrahedron slots allocated (bounds of every id read from the mesh)
   uint32_t npts;   // vertex slots allocated
+  float4* subdet;  // sub-determinant cache of the asynchronous engine (two float4 per slot) or
+                   // null; the engines that do not fill it mark the entries they replace invalid
 };
 
 // Claim priority of point p in the current round. Section 3.2 settles conflicts by a total
@@ -620,6 +622,7 @@ static __device__ int insert_warp(const Ctx& c, const InsWS& w, uint32_t p, unsi
     dst[1] = w.nn[i];
     uint32_t out = w.outh[i];
     reinterpret_cast<uint32_t*>(&c.tets[out].n)[w.ipos[i] >> 2] = s;
+    if (c.subdet) c.subdet[2 * (size_t)s + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   // cavity slots left over (|C| > |B|) die and join the free list after the round
   int freed = nc - nb;
@@ -806,6 +809,7 @@ static __device__ bool init_mesh(const Ctx& c, uint32_t vbegin, uint32_t vend, u
   for (int t = 0; t < 5; ++t) {
     c.tets[tbase + t].v = make_uint4(tv[t][0], tv[t][1], tv[t][2], tv[t][3]);
     c.tets[tbase + t].n = make_uint4(nn[t][0], nn[t][1], nn[t][2], nn[t][3]);
+    if (c.subdet) c.subdet[2 * (size_t)(tbase + t) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   vflag[i0] = vflag[i1] = vflag[i2] = vflag[i3] = 2;
   c.st->bump = tbase + 5;

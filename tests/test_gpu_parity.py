@@ -266,17 +266,20 @@ def test_errors_are_reported_not_raised_on_device():
 
 
 # ----------------------------------------------------------------------------- both engines
-@pytest.mark.parametrize("engine", ["async", "rounds"])
+@pytest.mark.parametrize("engine", ["async", "rounds", "async_subdet"])
 @pytest.mark.parametrize("kind,n,seed", [("uniform", 60000, 21), ("degenerate", 30000, 22), ("slab", 40000, 23)])
 def test_each_engine_alone_is_bit_exact(monkeypatch, engine, kind, n, seed):
     """The asynchronous engine (per-warp segments under ownership words) and the round-based one
     (claim words, three kernels a round) each give the oracle's tetrahedra on their own: DT_ASYNC=0
     keeps every pass on the rounds; DT_ASYNC_MIN_RETRY=1 sends even short retry lists to the
-    asynchronous engine."""
+    asynchronous engine. DT_SUBDET=1 runs the asynchronous engine's conflict tests through the
+    sub-determinant cache (the ablation of Section 2.4)."""
     if engine == "rounds":
         monkeypatch.setenv("DT_ASYNC", "0")
     else:
         monkeypatch.setenv("DT_ASYNC_MIN_RETRY", "1")
+    if engine == "async_subdet":
+        monkeypatch.setenv("DT_SUBDET", "1")
     x = synth.make(kind, n, seed)
     ref, _ = oracle.delaunay(x, seed=seed)
     got, st = gpu_tets(x, seed=seed)

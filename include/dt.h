@@ -133,7 +133,9 @@ int dt_create(dt_handle** out, const dt_config* cfg);
  * Stream-ordered on cfg->stream; returns after the triangulation is complete. */
 int dt_insert(dt_handle* h, const double* xyz_dev, uint64_t n);
 
-/* Same as dt_insert, with host input: the points are copied to the device inside the call. */
+/* Same as dt_insert, with host input: the points are copied to the device inside the call, into
+ * a device buffer the handle keeps for later calls (n * 24 bytes, freed by dt_destroy; counted
+ * in dt_stats.device_bytes). Page-locked host memory makes the copy fastest. */
 int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n);
 
 /* Triangulates n_clouds independent clouds: one batched sort (each cloud gets its own box,
@@ -210,7 +212,10 @@ int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets
  * DT_ESTATE after dt_batch; DT_ENOMEM if the scratch (n_points bytes) cannot be allocated. */
 int dt_check(dt_handle* h, uint64_t* out_host);
 
-/* Host variant of dt_get_tets: tets_host is host memory. */
+/* Host variant of dt_get_tets: tets_host is host memory ([cap, 4] uint32). The tetrahedra are
+ * collected once into a device buffer the handle keeps (cap * 16 bytes, freed by dt_destroy;
+ * counted in dt_stats.device_bytes) and copied out in one transfer (fastest into page-locked
+ * memory). cap = 0 only counts. DT_ETOOSMALL (with *n_tets the count) if cap is too small. */
 int dt_get_tets_host(dt_handle* h, uint32_t* tets_host, uint64_t cap, uint64_t* n_tets, int canonical);
 
 /* The sort of the last dt_insert call (Section 2.3): keys_dev[i] = 63-bit Moore key of input

@@ -290,10 +290,23 @@ class Triangulation:
     def tets_numpy(self, canonical: bool = True) -> np.ndarray:
         return self.tets(canonical).cpu().numpy().view(np.uint32)
 
-    def tets_host(self, canonical: bool = True) -> np.ndarray:
+    def tets_host(self, canonical: bool = True, out=None) -> np.ndarray:
+        """Finite tetrahedra as a host uint32 array [T, 4] (dt_get_tets_host). out: a C-contiguous
+        uint32 [rows, 4] host array to fill (page-locked memory copies fastest); a new array
+        is allocated when it is None or too small."""
+        n = ctypes.c_uint64()
+        if out is not None:
+            if not (isinstance(out, np.ndarray) and out.dtype == np.uint32 and out.ndim == 2
+                    and out.shape[1] == 4 and out.flags.c_contiguous):
+                raise TypeError("out must be a C-contiguous uint32 array [rows, 4]")
+            rc = lib().dt_get_tets_host(self._h, out.ctypes.data_as(ctypes.c_void_p), out.shape[0],
+                                        ctypes.byref(n), 1 if canonical else 0)
+            if rc == DT_OK:
+                return out[: n.value]
+            if rc != DT_ETOOSMALL:
+                _check(rc, "dt_get_tets_host")
         T = self.num_tets()
         out = np.empty((max(T, 1), 4), dtype=np.uint32)
-        n = ctypes.c_uint64()
         _check(lib().dt_get_tets_host(self._h, out.ctypes.data_as(ctypes.c_void_p), T, ctypes.byref(n),
                                       1 if canonical else 0), "dt_get_tets_host")
         return out[: n.value]

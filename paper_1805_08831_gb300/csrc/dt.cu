@@ -881,6 +881,10 @@ struct dt_handle {
   unsigned long long* claim = nullptr;
   uint32_t* lock = nullptr;  // asynchronous engine: owner of each slot (0 = free)
   float4* subdet = nullptr;  // sub-determinant cache (ablation, DT_SUBDET=1): two float4 per slot
+  double* in_buf = nullptr;    // dt_insert_host: the device copy of the host points, kept between calls
+  uint64_t in_cap = 0;         // rows
+  uint32_t* out_buf = nullptr; // dt_get_tets_host: the tetrahedra on the device before the copy out
+  uint64_t out_cap = 0;        // rows
   bool use_subdet = false;
   uint64_t cap_tets = 0;
   uint32_t* freelist = nullptr;
@@ -1068,6 +1072,7 @@ uint64_t device_bytes(const dt_handle* h) {
   b += h->cap_pts * (sizeof(Pt) + sizeof(PtF) + 1 + 4);             // points, FP32 copy, flag, hint
   b += h->cap_tets * (sizeof(Tet) + 16 + 4);                         // records, claim pair, owner word
   if (h->subdet) b += h->cap_tets * 2 * sizeof(float4);              // sub-determinant cache
+  b += h->in_cap * 24 + h->out_cap * 16;                             // host entry points' buffers
   b += h->cap_free * 8;                                              // free list and pending
   if (h->cell_hint_cb > 0) {
     const int cb = h->cell_hint_cb, cbc = cb > 3 ? cb - 3 : 1;
@@ -2366,8 +2371,15 @@ int dt_refine(dt_handle* h, double size, double ratio, double spacing, const dou
     // fill an empty interior (cavities of thousands of tetrahedra): the round-based engine,
     // with its full predicate cascade and large-cavity tiers, is faster here (5.9 s against
     // 10.9 s for the 1/128 box)
-    if (h->refine_rebuild > 0 && (double)ns >= h->refine_rebuild * (double)h->n_pts)
+    // a rebuild pays for the whole mesh again (the boundary points' degenerate predicates
+    // included) but keeps every cavity small; inserting a quarter of the mesh's points or more
+    // into it measured slower than rebuilding at every iteration of the 1/128 box (requiring
+    // also as many new points as refinement had added so far: 1.90 s against 1.75 s)
+    if (h->refine_rebuild > 0 && (double)ns >= h->refine_rebuild * (double)h->n_pts) {
+      h->alpha = alpha_keep;  // a rebuild is a plain insertion of the whole set
       rc = rebuild_with(h, h->rws.xyz, ns, h->refine_rebuild_async);
+      h->alpha = h->alpha_refine;
+    }
     else
       rc = insert_impl(h, h->rws.xyz, ns, false);
     if (rc != DT_OK) break;
@@ -2432,15 +2444,19 @@ int dt_check(dt_handle* h, uint64_t* out_host) {
 int dt_insert_host(dt_handle* h, const double* xyz_host, uint64_t n) {
   if (!h || (n > 0 && !xyz_host)) return DT_EINVAL;
   if (h->batch_mode) return DT_ESTATE;
-  double* d = nullptr;
-  if (n && cudaMalloc(&d, n * 24) != cudaSuccess) return DT_ENOMEM;
-  if (n && cudaMemcpyAsync(d, xyz_host, n * 24, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
-    cudaFree(d);
-    return DT_ECUDA;
+  // the device copy lives in a buffer the handle keeps, so a call allocates only when it grows
+  if (n > h->in_cap) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->in_buf);
+    h->in_buf = nullptr;
+    h->in_cap = 0;
+    if (cudaMalloc(&h->in_buf, n * 24) != cudaSuccess) return DT_ENOMEM;
+    h->in_cap = n;
   }
-  int rc = insert_impl(h, d, n);
+  if (n && cudaMemcpyAsync(h->in_buf, xyz_host, n * 24, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return DT_ECUDA;
+  int rc = insert_impl(h, h->in_buf, n);
   cudaStreamSynchronize(h->stream);
-  cudaFree(d);
   return rc;
 }
 
@@ -2470,12 +2486,16 @@ int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets
   unsigned long long* cnt = nullptr;
   uint32_t* tmp = nullptr;
   if (cudaMalloc(&cnt, 8) != cudaSuccess) return DT_ENOMEM;
-  if (cudaMalloc(&tmp, std::max<uint64_t>(slots, 1) * 16) != cudaSuccess) {
+  // the sorted list needs the unsorted one first; otherwise the tetrahedra go straight to the
+  // caller's buffer (a count alone when it has none)
+  const bool sort = canonical && !(h->cfg.flags & DT_FLAG_NO_CANONICAL_SORT) && cap > 0;
+  if (sort && cudaMalloc(&tmp, std::max<uint64_t>(slots, 1) * 16) != cudaSuccess) {
     cudaFree(cnt);
     return DT_ENOMEM;
   }
   cudaMemsetAsync(cnt, 0, 8, s);
-  k_collect<<<grid_for(slots, 256), 256, 0, s>>>(h->tets, slots, h->pts, h->cap_pts, tmp, cnt, slots, canonical);
+  k_collect<<<grid_for(slots, 256), 256, 0, s>>>(h->tets, slots, h->pts, h->cap_pts, sort ? tmp : tets_dev, cnt,
+                                                 sort ? slots : cap, canonical);
   ++g_kernel_launches;
   unsigned long long T = 0;
   cudaMemcpyAsync(&T, cnt, 8, cudaMemcpyDeviceToHost, s);
@@ -2487,7 +2507,7 @@ int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets
     cudaFree(tmp);
     return DT_ETOOSMALL;
   }
-  if (canonical && !(h->cfg.flags & DT_FLAG_NO_CANONICAL_SORT) && T > 1) {
+  if (sort && T > 1) {
     uint64_t *khi = nullptr, *klo = nullptr, *ka = nullptr;
     uint32_t *idx = nullptr, *ia = nullptr, *hist = nullptr;
     bool ok = cudaMalloc(&khi, T * 8) == cudaSuccess && cudaMalloc(&klo, T * 8) == cudaSuccess &&
@@ -2514,7 +2534,7 @@ int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets
     cudaFree(idx);
     cudaFree(ia);
     cudaFree(hist);
-  } else if (T) {
+  } else if (sort && T) {
     cudaMemcpyAsync(tets_dev, tmp, T * 16, cudaMemcpyDeviceToDevice, s);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) rc = DT_ECUDA;
@@ -2525,18 +2545,24 @@ int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets
 
 int dt_get_tets_host(dt_handle* h, uint32_t* tets_host, uint64_t cap, uint64_t* n_tets, int canonical) {
   if (!h || !n_tets || (cap > 0 && !tets_host)) return DT_EINVAL;
+  *n_tets = 0;
+  if (cap == 0) return dt_get_tets(h, nullptr, 0, n_tets, nullptr, canonical);
+  // one collection into a device buffer kept by the handle, then one copy out (fast from
+  // page-locked memory)
+  if (cap > h->out_cap) {
+    cudaFree(h->out_buf);
+    h->out_buf = nullptr;
+    h->out_cap = 0;
+    if (cudaMalloc(&h->out_buf, cap * 16) != cudaSuccess) return DT_ENOMEM;
+    h->out_cap = cap;
+  }
   uint64_t T = 0;
-  int rc = dt_get_tets(h, nullptr, 0, &T, nullptr, canonical);
+  int rc = dt_get_tets(h, h->out_buf, cap, &T, nullptr, canonical);
   *n_tets = T;
-  if (rc != DT_OK && rc != DT_ETOOSMALL) return rc;
-  if (T > cap) return DT_ETOOSMALL;
-  if (T == 0) return DT_OK;
-  uint32_t* d = nullptr;
-  if (cudaMalloc(&d, T * 16) != cudaSuccess) return DT_ENOMEM;
-  rc = dt_get_tets(h, d, T, &T, nullptr, canonical);
-  if (rc == DT_OK && cudaMemcpy(tets_host, d, T * 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = DT_ECUDA;
-  cudaFree(d);
-  return rc;
+  if (rc != DT_OK) return rc;
+  if (T && cudaMemcpyAsync(tets_host, h->out_buf, T * 16, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return DT_ECUDA;
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? DT_OK : DT_ECUDA;
 }
 
 int dt_get_order(dt_handle* h, uint64_t* keys_dev, uint32_t* perm_dev, uint8_t* rounds_dev) {
@@ -2629,6 +2655,8 @@ void dt_destroy(dt_handle* h) {
   cudaFree(h->claim);
   cudaFree(h->lock);
   cudaFree(h->subdet);
+  cudaFree(h->in_buf);
+  cudaFree(h->out_buf);
   cudaFree(h->async_big_ws);
   cudaFree(h->async_borrow_ws);
   cudaFree(h->async_borrow_busy);

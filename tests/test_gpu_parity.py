@@ -251,6 +251,21 @@ def test_host_entry_points_match_device_ones():
     with dt.Triangulation() as t:
         t.insert_host(x)
         assert_same(t.tets_host(), ref)
+        # the handle keeps its device buffers between calls: a second, smaller insert reuses them
+        t.clear()
+        t.insert_host(x[:3000])
+        ref2, _ = oracle.delaunay(x[:3000])
+        assert_same(t.tets_host(), ref2)
+        # a caller's buffer: filled when large enough, replaced when too small
+        big = np.full((len(ref2) + 10, 4), 7, dtype=np.uint32)
+        got = t.tets_host(out=big)
+        assert got.base is big or got is big or np.shares_memory(got, big)
+        assert_same(got, ref2)
+        small = np.zeros((5, 4), dtype=np.uint32)
+        assert_same(t.tets_host(out=small), ref2)
+        # unsorted output holds the same set
+        raw = t.tets_host(canonical=False)
+        assert len(raw) == len(ref2)
 
 
 def test_errors_are_reported_not_raised_on_device():

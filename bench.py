@@ -873,7 +873,7 @@ def main():
         # one plain launch sequence per cloud, the 1e8 scale, the learned schedule against the
         # plain one on the 1e8 cube + slab, and Delaunay refinement of a box
         import argparse as _ap
-        bargs = _ap.Namespace(clouds=args.clouds, steps=3, warmup=2, e2e_steps=0, plain_sample=32,
+        bargs = _ap.Namespace(clouds=args.clouds, steps=3, warmup=2, e2e_steps=2, plain_sample=32,
                               no_cpu_baseline=True)
         bl = run_batch(bargs, rank, world, local, None)
         line["batch"] = {"workload": bl["config"]["workload"], "value": bl["value"], "unit": "Mtets/s",
@@ -881,7 +881,8 @@ def main():
                          "plain_per_cloud": bl["plain_per_cloud"]["value"],
                          "batched_over_plain": bl["batched_over_plain"], "roofline_frac": bl["roofline"]["frac"],
                          "shape": [bl["config"]["batch_warps"], bl["config"]["batch_min_blocks"],
-                                   bl["config"]["batch_alpha"]], "graph_replay": bl["config"]["graph_replay"]}
+                                   bl["config"]["batch_alpha"]], "graph_replay": bl["config"]["graph_replay"],
+                         "e2e": bl["e2e"]}
         line["scale_1e8"] = scale_run("uniform", 1e8, SEED, 2, 1)
         line["scale_3e8"] = scale_certified(3e8, SEED, 1, 1)
         line["ablation_subdet"] = subdet_ablation(n, SEED, args.steps, args.warmup, value)

@@ -212,10 +212,12 @@ int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets
  * DT_ESTATE after dt_batch; DT_ENOMEM if the scratch (n_points bytes) cannot be allocated. */
 int dt_check(dt_handle* h, uint64_t* out_host);
 
-/* Host variant of dt_get_tets: tets_host is host memory ([cap, 4] uint32). The tetrahedra are
- * collected once into a device buffer the handle keeps (cap * 16 bytes, freed by dt_destroy;
- * counted in dt_stats.device_bytes) and copied out in one transfer (fastest into page-locked
- * memory). cap = 0 only counts. DT_ETOOSMALL (with *n_tets the count) if cap is too small. */
+/* Host variant of dt_get_tets: tets_host is host memory ([cap, 4] uint32). Without the
+ * canonical sort, page-locked memory (cudaHostAlloc, cudaHostRegister) receives the rows
+ * straight from the collecting kernel through its mapped device address. Otherwise the
+ * tetrahedra are collected once into a device buffer the handle keeps (cap * 16 bytes, freed by
+ * dt_destroy; counted in dt_stats.device_bytes) and copied out in one transfer. cap = 0 only
+ * counts. DT_ETOOSMALL (with *n_tets the count) if cap is too small. */
 int dt_get_tets_host(dt_handle* h, uint32_t* tets_host, uint64_t cap, uint64_t* n_tets, int canonical);
 
 /* The sort of the last dt_insert call (Section 2.3): keys_dev[i] = 63-bit Moore key of input

@@ -274,7 +274,9 @@ __device__ __forceinline__ int walk_async(const Ctx& c, uint32_t p, const PtF& F
       o = get4(T.n, lane) == prev ? 1 : orient_with_p(c, lane, FP, F0, F1, F2, F3);
     }
     const unsigned sees = __ballot_sync(kFull, lane < 4 && o < 0) & 0xFu;
-    if (__ballot_sync(kFull, lane < 4 && o == 0) & 0xFu) return kAExact;
+    // a facet the FP32 stage cannot decide matters only when no other facet is certainly seen:
+    // any facet p sees is a valid exit of the visibility walk
+    if (sees == 0 && (__ballot_sync(kFull, lane < 4 && o == 0) & 0xFu)) return kAExact;
     if (sees == 0) {
       // p is inside (or on) this tetrahedron: a vertex equal to p would be a duplicate
       bool dup = false;

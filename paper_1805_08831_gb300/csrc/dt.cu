@@ -577,19 +577,38 @@ __global__ void k_build_pts(const double* __restrict__ xyz, const uint32_t* __re
 }
 
 // Finite live tetrahedra with vertex ids mapped to input indices; canonical rotation optional.
+// One counter update per warp and iteration (ballot, then each lane's rank among the warp's
+// kept tetrahedra): a warp's rows land next to each other, and the counter sees 32 times fewer
+// atomics. The grid-stride loop runs the same number of times on every lane of a warp.
 __global__ void k_collect(const Tet* __restrict__ tets, uint64_t nslots, const Pt* __restrict__ pts,
                           uint64_t npts, uint32_t* out, unsigned long long* count, uint64_t cap,
                           int canonical) {
-  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nslots;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    uint4 v = tets[t].v;
-    if (tet_dead(v) || ghost_pos(v) >= 0) continue;
-    if (v.x >= npts || v.y >= npts || v.z >= npts || v.w >= npts) continue;
-    uint32_t r[4] = {(uint32_t)pts[v.x].w, (uint32_t)pts[v.y].w, (uint32_t)pts[v.z].w, (uint32_t)pts[v.w].w};
-    if (canonical) canonical_rotation(r);
-    unsigned long long pos = atomicAdd(count, 1ull);
-    if (pos < cap) {
-      reinterpret_cast<uint4*>(out)[pos] = make_uint4(r[0], r[1], r[2], r[3]);
+  const int lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) - lane;
+  for (uint64_t base = warp0; base < nslots; base += stride) {
+    const uint64_t t = base + lane;
+    bool keep = false;
+    uint32_t r[4] = {0, 0, 0, 0};
+    if (t < nslots) {
+      const uint4 v = tets[t].v;
+      keep = !tet_dead(v) && ghost_pos(v) < 0 && v.x < npts && v.y < npts && v.z < npts && v.w < npts;
+      if (keep) {
+        r[0] = (uint32_t)pts[v.x].w;
+        r[1] = (uint32_t)pts[v.y].w;
+        r[2] = (uint32_t)pts[v.z].w;
+        r[3] = (uint32_t)pts[v.w].w;
+        if (canonical) canonical_rotation(r);
+      }
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+    if (m == 0) continue;
+    unsigned long long first = 0;
+    if (lane == 0) first = atomicAdd(count, (unsigned long long)__popc(m));
+    first = __shfl_sync(0xFFFFFFFFu, first, 0);
+    if (keep) {
+      const unsigned long long pos = first + __popc(m & ((1u << lane) - 1u));
+      if (pos < cap) reinterpret_cast<uint4*>(out)[pos] = make_uint4(r[0], r[1], r[2], r[3]);
     }
   }
 }
@@ -2547,6 +2566,18 @@ int dt_get_tets_host(dt_handle* h, uint32_t* tets_host, uint64_t cap, uint64_t* 
   if (!h || !n_tets || (cap > 0 && !tets_host)) return DT_EINVAL;
   *n_tets = 0;
   if (cap == 0) return dt_get_tets(h, nullptr, 0, n_tets, nullptr, canonical);
+  // page-locked host memory is mapped into the device's address space: without the canonical
+  // sort the collection writes the rows there directly, and no copy follows
+  const bool sort = canonical && !(h->cfg.flags & DT_FLAG_NO_CANONICAL_SORT);
+  cudaPointerAttributes at{};
+  if (!sort && cudaPointerGetAttributes(&at, tets_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer) {
+    uint64_t T = 0;
+    const int rc = dt_get_tets(h, static_cast<uint32_t*>(at.devicePointer), cap, &T, nullptr, canonical);
+    *n_tets = T;
+    return rc;
+  }
+  cudaGetLastError();  // a pointer the runtime does not know leaves an error behind; it is not one
   // one collection into a device buffer kept by the handle, then one copy out (fast from
   // page-locked memory)
   if (cap > h->out_cap) {

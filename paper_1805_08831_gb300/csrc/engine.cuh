@@ -177,13 +177,16 @@ __device__ __forceinline__ Pt self4d(int i, int k, const Pt& P, const Pt& V) { r
 
 // orient3d of tetrahedron vertices v[] with vertex i replaced by the query p (FP32 stage first).
 // v must be a finite tetrahedron: all four of its vertices are read on the FP64 path.
+// exact = false stops after the filters (FP32, then FP64) and returns 0 when they cannot decide.
 __device__ __forceinline__ int orient_replace(const Ctx& c, const uint4& v, int i, uint32_t p, const PtF& FP,
-                                              const PtF& F0, const PtF& F1, const PtF& F2, const PtF& F3) {
+                                              const PtF& F0, const PtF& F1, const PtF& F2, const PtF& F3,
+                                              bool exact = true) {
   int o = orient3d_f(self4(i, 0, FP, F0), self4(i, 1, FP, F1), self4(i, 2, FP, F2), self4(i, 3, FP, F3), c.eta);
   if (o != 0) return o;
   Pt P = load_pt(c.pts, p);
   Pt V0 = load_pt(c.pts, v.x), V1 = load_pt(c.pts, v.y), V2 = load_pt(c.pts, v.z), V3 = load_pt(c.pts, v.w);
-  return orient3d(self4d(i, 0, P, V0), self4d(i, 1, P, V1), self4d(i, 2, P, V2), self4d(i, 3, P, V3), c.st);
+  const Pt A = self4d(i, 0, P, V0), B = self4d(i, 1, P, V1), C = self4d(i, 2, P, V2), D = self4d(i, 3, P, V3);
+  return exact ? orient3d(A, B, C, D, c.st) : orient3d_filter(A, B, C, D);
 }
 
 // Returns kCandLocated (*t_out in conflict with p), kCandWalkLimit (*t_out = where it stopped)
@@ -231,14 +234,25 @@ static __device__ int walk_point(const Ctx& c, uint32_t p, const PtF& FP, uint32
         F3 = load_ptf(c.ptf, T.v.w);
     int exit = -1;
     int s0 = (salt + steps) & 3;
+    // the filters first: any facet p certainly sees is a valid exit, so the exact sign of a
+    // facet the filters cannot decide (p on or near its plane: lattices, surfaces) is needed
+    // only when no other facet is certainly seen
+    unsigned undecided = 0;
     for (int k = 0; k < 4; ++k) {
       int i = (s0 + k) & 3;
       uint32_t nb = get4(T.n, i);
       if (nb == prev) continue;  // p is on this tetrahedron's side of the facet just crossed
-      if (orient_replace(c, T.v, i, p, FP, F0, F1, F2, F3) < 0) {
+      const int o = orient_replace(c, T.v, i, p, FP, F0, F1, F2, F3, false);
+      if (o < 0) {
         exit = i;
         break;
       }
+      if (o == 0) undecided |= 1u << k;
+    }
+    for (int k = 0; k < 4 && exit < 0 && undecided; ++k) {
+      if (!(undecided & (1u << k))) continue;
+      const int i = (s0 + k) & 3;
+      if (orient_replace(c, T.v, i, p, FP, F0, F1, F2, F3) < 0) exit = i;
     }
     if (exit < 0) {
       bool dup = false;

@@ -567,7 +567,8 @@ __device__ __forceinline__ double absmax3(double a, double b, double c) {
   return fmax(fmax(fabs(a), fabs(b)), fabs(c));
 }
 
-__device__ __forceinline__ int orient3d(Pt a, Pt b, Pt c, Pt d, DevState* st) {
+// The FP64 filter of orient3d alone: the sign, or 0 when it cannot be certain.
+__device__ __forceinline__ int orient3d_filter(const Pt& a, const Pt& b, const Pt& c, const Pt& d) {
   double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
   double vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
   double wx = d.x - a.x, wy = d.y - a.y, wz = d.z - a.z;
@@ -579,7 +580,12 @@ __device__ __forceinline__ int orient3d(Pt a, Pt b, Pt c, Pt d, DevState* st) {
     if (det > eb) return 1;
     if (det < -eb) return -1;
   }
-  return orient3d_exact(a, b, c, d, st);
+  return 0;
+}
+
+__device__ __forceinline__ int orient3d(Pt a, Pt b, Pt c, Pt d, DevState* st) {
+  const int s = orient3d_filter(a, b, c, d);
+  return s != 0 ? s : orient3d_exact(a, b, c, d, st);
 }
 
 __device__ __forceinline__ double det3d(double ax, double ay, double az, double bx, double by,

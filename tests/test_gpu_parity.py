@@ -263,9 +263,16 @@ def test_host_entry_points_match_device_ones():
         assert_same(got, ref2)
         small = np.zeros((5, 4), dtype=np.uint32)
         assert_same(t.tets_host(out=small), ref2)
-        # unsorted output holds the same set
+        # unsorted output holds the same set, into pageable memory (a copy) or page-locked
+        # memory (written by the kernel through its mapped address)
         raw = t.tets_host(canonical=False)
-        assert len(raw) == len(ref2)
+        pinned = torch.zeros((len(ref2) + 3, 4), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        raw_pinned = t.tets_host(canonical=False, out=pinned)
+        for r in (raw, raw_pinned):
+            assert len(r) == len(ref2)
+            rot = np.sort(r, axis=1)
+            assert_same(rot[np.lexsort(rot.T[::-1])], (lambda q: q[np.lexsort(q.T[::-1])])(np.sort(ref2, axis=1)))
+        assert not pinned[len(ref2):].any()  # nothing written past the count
 
 
 def test_errors_are_reported_not_raised_on_device():

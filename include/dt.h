@@ -176,7 +176,10 @@ int dt_batch(dt_handle* h, const double* xyz_dev, const uint64_t* offsets_host, 
  *  - box_host: 6 float64 (host): lo x, y, z, hi x, y, z, lo < hi on every axis.
  * DT_EINVAL for a non-positive or non-finite size, ratio or spacing, a bad box, or a box wider
  * than 2^21 filter cells (spacing * size) per axis; DT_ESTATE without a triangulation or after
- * dt_batch. Insertion errors are returned as by dt_insert, with the counts reached so far. */
+ * dt_batch. Insertion errors are returned as by dt_insert, with the counts reached so far.
+ * An iteration that adds at least a quarter as many points as the mesh holds rebuilds the mesh
+ * from all its points (same input indices, so the same triangulation); after an error in that
+ * step the handle holds the part of the rebuild that was reached, as after a failed dt_insert. */
 int dt_refine(dt_handle* h, double size, double ratio, double spacing, const double* box_host, uint32_t max_iters,
               uint64_t* n_added, uint32_t* n_iters);
 

@@ -51,6 +51,16 @@ def test_refine_box_surface_matches_oracle(k):
     check_refined(P, tets, len(X), counts, 1.0 / k, UNIT)
 
 
+@pytest.mark.parametrize("rebuild", ["0", "0.25", "0.000001"])
+def test_refine_rebuilds_give_the_incremental_mesh(monkeypatch, rebuild):
+    """An iteration that adds many points may rebuild the mesh from all its points instead of
+    inserting into it (DT_REFINE_REBUILD: never, at a quarter of the mesh's points, at every
+    iteration); the triangulation is unique, so the points and the mesh equal the oracle's."""
+    monkeypatch.setenv("DT_REFINE_REBUILD", rebuild)
+    X = synth.box_surface(10)
+    assert_matches_oracle(X, 1.0 / 10)
+
+
 def test_refine_cloud_with_corners_matches_oracle():
     X = np.r_[synth.uniform_cube(1500, 8), CORNERS]
     P, tets, counts = assert_matches_oracle(X, 0.05)

@@ -190,7 +190,9 @@ int dt_refine(dt_handle* h, double size, double ratio, double spacing, const dou
 int dt_get_points(dt_handle* h, double* xyz_dev, uint64_t rows, uint64_t* n_points);
 
 /* Copies the finite tetrahedra of the current triangulation into tets_dev ([cap, 4] uint32,
- * device). canonical != 0 rotates and sorts them (see conventions); 0 writes them positively
+ * device memory, or page-locked host memory that the kernels write through its mapped device
+ * address; pageable host memory gives DT_EINVAL). canonical != 0 rotates and sorts them (see
+ * conventions); 0 writes them positively
  * oriented in an unspecified order. *n_tets receives the count; DT_ETOOSMALL if cap < count.
  * After dt_batch, cloud_offsets (host, n_clouds + 1 entries, may be NULL) receives where each
  * cloud's tetrahedra start; each cloud's block is canonical on its own. */

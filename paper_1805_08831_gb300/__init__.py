@@ -254,13 +254,25 @@ class Triangulation:
                                        off.ctypes.data_as(ctypes.c_void_p), off.size - 1), "dt_batch")
         self._n_clouds = off.size - 1
 
-    def tets_batch(self, canonical: bool = True):
+    def tets_batch(self, canonical: bool = True, out=None):
         """After batch(): (tets numpy uint32 [T, 4] with cloud-local ids, cloud_offsets numpy
-        uint64 [n_clouds + 1]); each cloud's rows are canonical on their own."""
+        uint64 [n_clouds + 1]); each cloud's rows are canonical on their own. out: a page-locked
+        host uint32 array [rows, 4] (e.g. from torch's pin_memory) that receives the rows
+        directly when it is large enough."""
         torch = _torch()
         nc = self._n_clouds
         coff = np.zeros(nc + 1, dtype=np.uint64)
         n = ctypes.c_uint64()
+        if out is not None:
+            if not (isinstance(out, np.ndarray) and out.dtype == np.uint32 and out.ndim == 2
+                    and out.shape[1] == 4 and out.flags.c_contiguous):
+                raise TypeError("out must be a C-contiguous uint32 array [rows, 4]")
+            rc = lib().dt_get_tets(self._h, out.ctypes.data_as(ctypes.c_void_p), out.shape[0], ctypes.byref(n),
+                                   coff.ctypes.data_as(ctypes.c_void_p), 1 if canonical else 0)
+            if rc == DT_OK:
+                return out[: n.value], coff
+            if rc not in (DT_ETOOSMALL, DT_EINVAL):  # DT_EINVAL: pageable memory, not written
+                _check(rc, "dt_get_tets")
         rc = lib().dt_get_tets(self._h, None, 0, ctypes.byref(n), coff.ctypes.data_as(ctypes.c_void_p), 0)
         if rc not in (DT_OK, DT_ETOOSMALL):
             _check(rc, "dt_get_tets")

@@ -2077,12 +2077,14 @@ int batch_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_t
   if (cloud_offsets)
     for (uint32_t c = 0; c <= nc; ++c) cloud_offsets[c] = oo[c];
   if (rc == DT_OK && T > cap) rc = DT_ETOOSMALL;
+  // the sorted list needs the unsorted one first; otherwise the rows go straight to the output
+  const bool sort = canonical && !(h->cfg.flags & DT_FLAG_NO_CANONICAL_SORT) && T > 1;
   uint32_t* tmp = nullptr;
-  if (rc == DT_OK && T > 0 && cudaMalloc(&tmp, T * 16) != cudaSuccess) rc = DT_ENOMEM;
+  if (rc == DT_OK && sort && cudaMalloc(&tmp, T * 16) != cudaSuccess) rc = DT_ENOMEM;
   if (rc == DT_OK && T > 0) {
     cudaMemcpyAsync(ooff, oo.data(), (nc + 1) * 8ull, cudaMemcpyHostToDevice, s);
-    batch_collect(h->bclouds, nc, h->tets, h->pts, h->boff_dev, 1, counts, ooff, tmp, canonical, s);
-    if (canonical && !(h->cfg.flags & DT_FLAG_NO_CANONICAL_SORT) && T > 1) {
+    batch_collect(h->bclouds, nc, h->tets, h->pts, h->boff_dev, 1, counts, ooff, sort ? tmp : tets_dev, canonical, s);
+    if (sort) {
       // lexicographic by (cloud, a, b, c, d): LSD passes on (c, d), then (a, b), then the cloud
       uint64_t *khi = nullptr, *klo = nullptr, *kcl = nullptr, *ka = nullptr;
       uint32_t *idx = nullptr, *ia = nullptr, *hist = nullptr;
@@ -2118,8 +2120,6 @@ int batch_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_t
       cudaFree(idx);
       cudaFree(ia);
       cudaFree(hist);
-    } else {
-      cudaMemcpyAsync(tets_dev, tmp, T * 16, cudaMemcpyDeviceToDevice, s);
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = DT_ECUDA;
   }
@@ -2496,6 +2496,18 @@ int dt_get_tets(dt_handle* h, uint32_t* tets_dev, uint64_t cap, uint64_t* n_tets
                 int canonical) {
   if (!h || !n_tets || (cap > 0 && !tets_dev)) return DT_EINVAL;
   *n_tets = 0;
+  if (cap > 0) {
+    // page-locked host memory is accepted too, through its mapped device address
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, tets_dev) == cudaSuccess) {
+      if (at.type == cudaMemoryTypeUnregistered) return DT_EINVAL;  // pageable host memory
+      if (at.type == cudaMemoryTypeHost) {
+        if (!at.devicePointer) return DT_EINVAL;
+        tets_dev = static_cast<uint32_t*>(at.devicePointer);
+      }
+    }
+    cudaGetLastError();  // an unknown pointer leaves an error behind; it is not one
+  }
   if (h->batch_mode) return batch_get_tets(h, tets_dev, cap, n_tets, cloud_offsets, canonical);
   if (!h->has_mesh) return DT_OK;
   cudaStream_t s = h->stream;

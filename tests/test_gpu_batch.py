@@ -89,6 +89,27 @@ def test_batch_equals_single_cloud_inserts():
         assert np.array_equal(got[c], single)
 
 
+def test_batch_output_into_page_locked_host_memory():
+    """Unsorted rows written by the collection kernel straight into page-locked host memory hold
+    each cloud's tetrahedra (the sorted device output, as sets); pageable memory is refused by
+    the C ABI and the binding falls back to its own array."""
+    xyz, off = synth.batched_clouds(12, 41, lo=50, hi=6000)
+    with dt.Triangulation(seed=3) as t:
+        t.batch(torch.from_numpy(xyz).cuda(), off)
+        ref, roff = t.tets_batch(canonical=True)
+        pinned = torch.zeros((len(ref) + 7, 4), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        got, goff = t.tets_batch(canonical=False, out=pinned)
+        assert np.shares_memory(got, pinned) and np.array_equal(goff, roff)
+        assert not pinned[len(ref):].any()
+        pageable, poff = t.tets_batch(canonical=False, out=np.zeros((len(ref), 4), dtype=np.uint32))
+        assert np.array_equal(poff, roff)
+    for res in (got, pageable):
+        for c in range(len(roff) - 1):
+            a = np.sort(res[int(roff[c]):int(roff[c + 1])], axis=1)
+            b = np.sort(ref[int(roff[c]):int(roff[c + 1])], axis=1)
+            assert np.array_equal(a[np.lexsort(a.T[::-1])], b[np.lexsort(b.T[::-1])])
+
+
 @pytest.mark.parametrize("warps", [8, 16, 32])
 def test_every_block_shape_gives_the_same_tets(warps, monkeypatch):
     monkeypatch.setenv("DT_BATCH_WARPS", str(warps))

@@ -9,7 +9,8 @@ library's stream; `e2e` repeats the step through the host entry points with the 
 Multi-GPU runs are replicas (one independent cloud per rank; a single cloud does not shard).
 The default line also carries the CPU legs (the serial oracle, and the paper's CPU thread scheme
 on every host core, both on the first 1e6 points) and the other rows of the path: the batched
-form, the learned schedule against the plain one, Delaunay refinement of a box, 1e8 and 5e8
+form, the learned schedule against the plain one, Delaunay refinement of a box, the 1e7
+degenerate mix, 1e8 and 5e8
 uniform points (the latter 3.4e9 tetrahedra, certified on the device by dt_check), and the
 sub-determinant caching ablation on the default workload.
 """
@@ -889,6 +890,9 @@ def main():
                                    bl["config"]["batch_alpha"]], "graph_replay": bl["config"]["graph_replay"],
                          "e2e": bl["e2e"]}
         line["scale_1e8"] = scale_run("uniform", 1e8, SEED, 2, 1)
+        # the degenerate mix (sphere, clusters, a lattice with duplicates), seed 3 as in the
+        # oracle's digests: the exact predicates and the round-based engine at scale
+        line["degenerate_1e7"] = scale_run("degenerate", 1e7, 3, 2, 1)
         # the paper's title figure: three billion tetrahedra (5e8 points, 3.4e9 tetrahedra) on one
         # GPU, with 7 tetrahedron slots per point (the run uses 6.77); 4e8 at the default 8 if
         # that does not fit beside this process's other allocations

@@ -2338,9 +2338,7 @@ int rebuild_with(dt_handle* h, const double* extra, uint64_t ns, bool allow_asyn
   if (rc == DT_OK &&
       cudaMemcpyAsync(all + 3 * n0, extra, ns * 24, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     rc = DT_ECUDA;
-  const dt_stats keep = h->stats;
   if (rc == DT_OK) rc = clear_mesh(h, true);
-  h->stats = keep;
   if (rc == DT_OK) rc = insert_impl(h, all, N, allow_async);
   cudaStreamSynchronize(h->stream);
   cudaFree(all);

@@ -217,6 +217,19 @@ def test_certificate_holds_where_the_oracle_agrees(kind, n, seed):
     assert st["n_unique"] == ost["n_unique"]
 
 
+def test_certificate_states():
+    """dt_check on a handle without a mesh counts nothing, and after a batch (whose clouds are
+    separate meshes) it is refused."""
+    with dt.Triangulation() as t:
+        assert t.check() == {"tets": 0, "bad_adjacency": 0, "bad_orientation": 0, "not_delaunay": 0,
+                             "vertices": 0}
+        xyz, off = synth.batched_clouds(3, 9, lo=50, hi=200)
+        t.batch(torch.from_numpy(xyz).cuda(), off)
+        with pytest.raises(dt.DTError) as e:
+            t.check()
+        assert e.value.code == dt.DT_ESTATE
+
+
 @pytest.mark.parametrize("name", sorted(DEGENERATE_SETS))
 def test_certificate_on_degenerate_sets(name):
     x = DEGENERATE_SETS[name]

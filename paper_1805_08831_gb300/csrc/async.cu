@@ -14,12 +14,16 @@
 //      (1) of Section 3.2: a thread touches only tetrahedra it owns);
 //   4. re-read C (whole records) and A (vertices) under the locks: a difference means another
 //      warp changed them between steps 2 and 3, and the insertion starts over from the walk;
+//      also read which facet of each tetrahedron of A faces the cavity (neighbour slots hold
+//      plain tetrahedron ids: it is the facet whose neighbour is the cavity tetrahedron);
 //   5. write the ball (Section 2.5: one tetrahedron per boundary facet, adjacency through the
 //      edge table), the back-pointers of A, then release every lock after a fence.
 // Aborted points wait in a small per-warp list and are retried after later insertions; what is
-// still left when the segment ends goes to the next pass. Cavities larger than the per-warp
-// workspace go to the large-cavity rounds. No warp ever waits on another, so every loop here
-// is bounded by the segment length and fixed retry counts.
+// still left when the segment ends goes to the next pass. A cavity larger than the per-warp
+// shared-memory workspace is inserted again in a global-memory workspace borrowed from a pool,
+// else by a separate large-cavity launch; a predicate the FP32 stage cannot decide hands the
+// point to the round-based engine. No warp ever waits on another, so every loop here is
+// bounded by the segment length and fixed retry counts.
 //
 // The triangulation does not depend on the order of insertions (exact predicates and one
 // symbolic perturbation, Section 2.4), so this engine gives the same tetrahedra as the

@@ -77,3 +77,24 @@ def test_path_bytes_are_the_tables_terms():
     terms, cfb = bench.path_bytes(st)
     assert cfb["V"] == 15.0 and cfb["w"] == 2.0
     assert terms == {"walk": 208.0, "cavity": 2824.0, "ball": 1200.0}
+
+
+def test_kernel_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The bench reports a captured DRAM traffic only while the kernel's sources hash the same;
+    a change of comments or blank lines keeps the hash, a change of code does not."""
+    import shutil
+
+    import bench
+    src = os.path.join(bench.ROOT, "paper_1805_08831_gb300", "csrc")
+    dst = tmp_path / "paper_1805_08831_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_sources_hash()
+    p = dst / "async.cu"
+    text = p.read_text()
+    p.write_text("// a new comment\n\n/* and a block\n   comment */\n" + text.replace("\n", "  // note\n", 3))
+    assert bench.kernel_sources_hash() == h0
+    p.write_text(text.replace("constexpr int kADefer = 16;", "constexpr int kADefer = 17;"))
+    assert bench.kernel_sources_hash() != h0
